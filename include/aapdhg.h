@@ -1,0 +1,185 @@
+/*
+ * aapdhg.h -- C ABI of the GB300 (sm_103a) AA-PDHG / FAA-PDHG LP solver.
+ *
+ * Method: arXiv 2508.08062.  The solver iterates the PDHG fixed-point map T
+ * (Sec. 3, eq. pdhg / eq. new-fixed-point) with Anderson acceleration in the
+ * regularised quasi-Newton form of Alg. 2 (AA-PDHG) or with the angle/length
+ * filters of Alg. 3-6 (FAA-PDHG), a safeguard, and a projection back onto
+ * X x Y.  Termination uses the relative KKT residual of the Remark on
+ * termination conditions.
+ *
+ * LP form (Sec. 2.1, eq. LP-O):
+ *     min c'x   s.t.  Gx >= h,  Ax = b,  l <= x <= u
+ * K = [G; A] is passed as one CSR matrix with one sense byte per row
+ * (AAPDHG_ROW_GE for a row of G, AAPDHG_ROW_EQ for a row of A), rows of
+ * either kind in any order, and q = [h; b] in the same row order (eq.
+ * lambda-case).  A "<=" row is passed negated as a ">=" row.
+ *
+ * Conventions of every entry point:
+ *  - Plain C types only; no C++ exception crosses the boundary.
+ *  - Host arrays passed in are copied; the caller keeps ownership.
+ *  - Output pointers are caller-owned host buffers of the stated length.
+ *  - Device memory of a handle is owned by the library and freed by
+ *    aapdhg_destroy; it comes from the allocator installed with
+ *    aapdhg_set_allocator (default cudaMalloc / cudaFree).
+ *  - All device work of a handle is ordered on the handle's CUDA stream.
+ *    A handle must not be used by two host threads at once.
+ *  - Errors are sticky: after a call returns an error other than
+ *    AAPDHG_NOT_CONVERGED, later calls on the handle return the same status
+ *    until aapdhg_destroy.  aapdhg_last_error gives a message.
+ */
+#ifndef AAPDHG_H
+#define AAPDHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct aapdhg_s *aapdhg_t;
+
+typedef enum {
+    AAPDHG_OK = 0,
+    AAPDHG_ERR_INVALID = 1,     /* bad argument or malformed CSR               */
+    AAPDHG_ERR_OOM = 2,         /* device allocation failed                     */
+    AAPDHG_ERR_CUDA = 3,        /* a CUDA runtime call failed                   */
+    AAPDHG_ERR_NUMERIC = 4,     /* NaN/Inf in the iterate or the KKT residual   */
+    AAPDHG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+    AAPDHG_NOT_CONVERGED = 6    /* iteration cap reached with KKT > tol         */
+} aapdhg_status;
+
+enum { AAPDHG_ROW_EQ = 0, AAPDHG_ROW_GE = 1 };
+enum { AAPDHG_FP64 = 0, AAPDHG_MIXED = 1 };     /* precision of iterates / SpMV   */
+enum { AAPDHG_PDHG = 0, AAPDHG_AA = 1, AAPDHG_FAA = 2 };
+enum { AAPDHG_MEM_HOST = 0, AAPDHG_MEM_DEVICE = 1 };
+enum { AAPDHG_MAX_MEMORY = 32 };                /* largest m_A                    */
+
+/* Device allocator used for every device buffer of handles created after the
+ * call (process-wide).  alloc returns NULL on failure.  Passing NULL for both
+ * restores cudaMalloc / cudaFree.  Always returns AAPDHG_OK.                  */
+typedef void *(*aapdhg_alloc_fn)(size_t bytes, void *ctx);
+typedef void (*aapdhg_free_fn)(void *ptr, void *ctx);
+aapdhg_status aapdhg_set_allocator(aapdhg_alloc_fn alloc, aapdhg_free_fn free_fn, void *ctx);
+
+/* Create a solver for the LP of eq. LP-O (Sec. 2.1).
+ *   m, n        rows of K (m1 + m2 >= 0) and variables (n >= 1)
+ *   nnz         entries of K, 0 <= nnz < 2^31
+ *   row_ptr     int64[m + 1], row_ptr[0] = 0, non-decreasing, row_ptr[m] = nnz
+ *   col_idx     int32[nnz], 0 <= col < n, no repeated column within a row
+ *   val         double[nnz], finite
+ *   row_sense   int8[m], AAPDHG_ROW_GE or AAPDHG_ROW_EQ
+ *   q           double[m] (h and b of eq. lambda-case), finite
+ *   c           double[n], finite
+ *   lb, ub      double[n], lb <= ub, -INFINITY / +INFINITY allowed (eq. LP-O)
+ *   precision   AAPDHG_FP64: iterates, SpMVs and reductions in FP64.
+ *               AAPDHG_MIXED: K, iterates, SpMVs and the Anderson memory in
+ *               FP32 with FP32 SpMV accumulation; Gram entries, the m x m
+ *               solve, the safeguard test and the KKT norms accumulate to
+ *               FP64 accuracy.
+ *   mem_kind    AAPDHG_MEM_HOST: the arrays above are host memory.
+ *               AAPDHG_MEM_DEVICE: they are device memory of the current device
+ *               (read once, before this call returns).
+ *   cuda_stream cudaStream_t for all work of the handle; NULL = a new
+ *               non-blocking stream owned by the handle.
+ *   out         receives the handle (NULL on error).
+ * The problem is validated (AAPDHG_ERR_INVALID on a malformed CSR, a
+ * non-finite value, lb > ub or an unknown sense) and copied to the device.
+ * Defaults after create: AA-PDHG with m_A = 5, D = 10, eps = 1, eta = 1e-10,
+ * beta = 1, c_s = 0.2, kappa = 1e8, c_div = 1, D-hat of the Remark, adaptive
+ * FAA memory; no step sizes (aapdhg_iterate fails until they are set);
+ * start x0 = P_X(0), y0 = 0.                                                  */
+aapdhg_status aapdhg_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col_idx, const double *val, const int8_t *row_sense,
+                            const double *q, const double *c, const double *lb, const double *ub,
+                            int32_t precision, int32_t mem_kind, void *cuda_stream,
+                            aapdhg_t *out);
+
+/* Step sizes tau, sigma of eq. pdhg.  Both must be finite and > 0; the
+ * convergence theory assumes sigma tau ||K||^2 < 1 (Assumption of Sec. 3),
+ * which the caller establishes (e.g. with aapdhg_estimate_norm).  Resets the
+ * run (as aapdhg_reset).                                                      */
+aapdhg_status aapdhg_set_steps(aapdhg_t h, double tau, double sigma);
+
+/* Estimate ||K||_2 by power iteration on K'K (the step-size rule of Sec. 5.1)
+ * with `iters` iterations from a seeded start vector; writes the estimate to
+ * *norm.  Uses the handle's stream and synchronises it.                       */
+aapdhg_status aapdhg_estimate_norm(aapdhg_t h, int32_t iters, uint64_t seed, double *norm);
+
+/* Method and Anderson parameters (Alg. 2 and Alg. 3-6):
+ *   method      AAPDHG_PDHG, AAPDHG_AA (Alg. 2) or AAPDHG_FAA (Alg. 3)
+ *   m_A         memory, 0 <= m_A <= AAPDHG_MAX_MEMORY (0: never accelerates)
+ *   D, eps      safeguard ||g^k|| <= D ||g^0|| (i^k / c_div + 1)^-(1+eps), D > 0, eps > 0
+ *   eta         Tikhonov parameter of Alg. 2 (>= 0; unused by FAA)
+ *   beta        damping in (0, 1]
+ *   c_s, kappa  angle / length filter thresholds of Alg. 4 / 5 (0 < c_s <= 1, kappa > 0)
+ *   c_div       safeguard divisor >= 1 (1 is Alg. 2; 3 is the "Iter_AA / c" variant)
+ *   dhat_mode   0: D-hat = I; 1: D-hat of the Remark on its construction
+ *   faa_adaptive 1: columns removed by the filters leave the memory (the
+ *               implemented variant of Sec. 5); 0: the filters act on a copy
+ * Resets the run (as aapdhg_reset).                                           */
+aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double D, double eps,
+                                double eta, double beta, double c_s, double kappa, double c_div,
+                                int32_t dhat_mode, int32_t faa_adaptive);
+
+/* Start point u^0 = (x0, y0) (host arrays of n and m doubles, or NULL for the
+ * default x0 = P_X(0), y0 = 0).  The start is projected onto X x Y, as Alg. 2
+ * asks for a feasible start.  Resets the run.                                 */
+aapdhg_status aapdhg_set_start(aapdhg_t h, const double *x0, const double *y0);
+
+/* Forget the run: the next aapdhg_iterate starts again from u^0 with an empty
+ * Anderson memory and zero counters.                                          */
+aapdhg_status aapdhg_reset(aapdhg_t h);
+
+/* Run at most max_iters loop iterations of Alg. 2 / Alg. 3 (resumable: a
+ * later call continues from the current iterate and memory).  The first call
+ * after a reset also forms u^1 = T u^0 and g^0 (not counted as an iteration).
+ * Every kkt_every-th iteration (counted over the whole run, first at
+ * iteration 0; kkt_every <= 0 disables the test) the KKT residual of the
+ * current iterate u^k is evaluated before T(u^k) is used; the run stops at u^k
+ * when it is <= tol.  *iters_done (may be NULL) receives the iterations done
+ * by this call.  Returns AAPDHG_OK when the tolerance was met (now or in an
+ * earlier call), AAPDHG_NOT_CONVERGED when max_iters ran out, or an error.    */
+aapdhg_status aapdhg_iterate(aapdhg_t h, int64_t max_iters, double tol, int32_t kkt_every,
+                             int64_t *iters_done);
+
+/* Current iterate u^k: x (n doubles) and y (m doubles) in the caller's row and
+ * column order; either pointer may be NULL.                                   */
+aapdhg_status aapdhg_get_iterate(aapdhg_t h, double *x, double *y);
+
+/* KKT quantities of the current iterate (Remark on termination conditions),
+ * evaluated now: out[0..5] = {r_p, r_d, r_g, KKT, c'x, dual objective}, with
+ * lambda = P_Lambda(c - K'y).                                                 */
+aapdhg_status aapdhg_get_kkt(aapdhg_t h, double *out6);
+
+/* Counters of the run: i (AA steps taken), j (PDHG steps taken), iterations,
+ * and AA steps rejected because the m x m factorisation failed (counted in
+ * j).  Any pointer may be NULL.                                               */
+aapdhg_status aapdhg_get_counters(aapdhg_t h, int64_t *aa_steps, int64_t *pdhg_steps,
+                                  int64_t *iters, int64_t *ls_failures);
+
+/* Per-iteration trace for the first `capacity` iterations of the next run
+ * (capacity 0 disables; resets the run).  aapdhg_get_trace copies up to
+ * *len entries: branch (0 PDHG step, 1 AA step, 2 AA step rejected by a failed
+ * factorisation), ||g^k||, KKT(u^k) (NaN when not evaluated) and the number
+ * of memory columns used by an accepted AA step (-1 otherwise).  Any output
+ * pointer may be NULL; *len receives the entries written.                     */
+aapdhg_status aapdhg_set_trace(aapdhg_t h, int64_t capacity);
+aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double *gnorm,
+                               double *kkt, int32_t *mk);
+
+/* Bytes of device memory held by the handle.                                 */
+aapdhg_status aapdhg_device_bytes(aapdhg_t h, int64_t *bytes);
+
+/* Message of the last error of the handle (or of the last failed create when
+ * h is NULL).  The string lives until the next call on the handle.            */
+const char *aapdhg_last_error(aapdhg_t h);
+
+/* Free the handle and its device memory (synchronises its stream).          */
+void aapdhg_destroy(aapdhg_t h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* AAPDHG_H */

@@ -1,0 +1,7 @@
+"""GB300-native (sm_103a) AA-PDHG / FAA-PDHG solver for linear programs (arXiv 2508.08062).
+
+The solver lives in the CUDA library ``libaapdhg.so`` (C ABI: ``include/aapdhg.h``);
+``binding`` is a thin ctypes wrapper over it.  Build with ``build.build()``.
+"""
+from .binding import (AA, FAA, FP64, MIXED, PDHG, AAPDHGError, Solver, load,  # noqa: F401
+                      use_torch_allocator)

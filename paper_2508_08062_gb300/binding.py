@@ -1,0 +1,251 @@
+"""Thin ctypes binding of the C ABI in ``include/aapdhg.h``.
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+``libaapdhg.so``.  PyTorch supplies the device memory (its caching allocator is
+installed as the library's allocator) and the CUDA stream (the current torch
+stream by default).  There is no CPU fallback: if the library is missing or no
+GPU is present, construction raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libaapdhg.so")
+
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, NOT_CONVERGED = range(7)
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NUMERIC",
+                5: "ERR_TIMEOUT", 6: "NOT_CONVERGED"}
+ROW_EQ, ROW_GE = 0, 1
+FP64, MIXED = 0, 1
+PDHG, AA, FAA = 0, 1, 2
+MEM_HOST, MEM_DEVICE = 0, 1
+METHODS = {"pdhg": PDHG, "aa": AA, "faa": FAA}
+PRECISIONS = {"fp64": FP64, "mixed": MIXED}
+
+# every entry point declared in include/aapdhg.h
+EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_estimate_norm",
+           "aapdhg_set_method", "aapdhg_set_start", "aapdhg_reset", "aapdhg_iterate",
+           "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
+           "aapdhg_get_trace", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
+
+
+class AAPDHGError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+_alloc_cb = None
+_free_cb = None
+
+
+def load(path: str = LIB_PATH):
+    """Load the CUDA library (raises when it is missing: no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    L = C.CDLL(path)
+    vp, i32, i64, f64 = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    st = C.c_int
+    L.aapdhg_set_allocator.argtypes = [vp, vp, vp]
+    L.aapdhg_create.argtypes = [i32, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, i32, i32, vp,
+                                C.POINTER(vp)]
+    L.aapdhg_set_steps.argtypes = [vp, f64, f64]
+    L.aapdhg_estimate_norm.argtypes = [vp, i32, C.c_uint64, C.POINTER(f64)]
+    L.aapdhg_set_method.argtypes = [vp, i32, i32, f64, f64, f64, f64, f64, f64, f64, i32, i32]
+    L.aapdhg_set_start.argtypes = [vp, vp, vp]
+    L.aapdhg_reset.argtypes = [vp]
+    L.aapdhg_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
+    L.aapdhg_get_iterate.argtypes = [vp, vp, vp]
+    L.aapdhg_get_kkt.argtypes = [vp, vp]
+    L.aapdhg_get_counters.argtypes = [vp, vp, vp, vp, vp]
+    L.aapdhg_set_trace.argtypes = [vp, i64]
+    L.aapdhg_get_trace.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
+    L.aapdhg_device_bytes.argtypes = [vp, C.POINTER(i64)]
+    L.aapdhg_last_error.argtypes = [vp]
+    L.aapdhg_last_error.restype = C.c_char_p
+    L.aapdhg_destroy.argtypes = [vp]
+    L.aapdhg_destroy.restype = None
+    for name in EXPORTS:
+        if name not in ("aapdhg_last_error", "aapdhg_destroy"):
+            getattr(L, name).restype = st
+    _lib = L
+    return L
+
+
+def use_torch_allocator():
+    """Route the library's device allocations through torch's caching allocator."""
+    global _alloc_cb, _free_cb
+    import torch
+    L = load()
+    ALLOC = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+    FREE = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+    def _alloc(nbytes, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev,
+                                                      torch.cuda.current_stream(dev))
+        except Exception:
+            return None
+
+    def _free(ptr, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    _alloc_cb, _free_cb = ALLOC(_alloc), FREE(_free)
+    L.aapdhg_set_allocator(C.cast(_alloc_cb, C.c_void_p), C.cast(_free_cb, C.c_void_p), None)
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    assert a.shape == (n,), (a.shape, n)
+    return a
+
+
+class Solver:
+    """One LP on the GPU (a handle of the C ABI).
+
+    ``problem`` is any object with m, n, row_ptr, col_idx, val, sense, q, c, l, u
+    (e.g. ``lpgen.Problem``).  ``device_inputs``: pass torch CUDA tensors as the
+    attributes instead (int64 row_ptr, int32 col_idx, float64 values, int8 sense).
+    """
+
+    def __init__(self, problem, precision: str = "mixed", stream=None, torch_memory: bool = True,
+                 device_inputs: bool = False):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        L = load()
+        if torch_memory:
+            use_torch_allocator()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._L = L
+        self._h = C.c_void_p()
+        self.m, self.n = int(problem.m), int(problem.n)
+        if device_inputs:
+            def dp(t):
+                return C.c_void_p(t.data_ptr())
+            nnz = int(problem.val.numel())
+            args = [dp(problem.row_ptr), dp(problem.col_idx), dp(problem.val), dp(problem.sense),
+                    dp(problem.q), dp(problem.c), dp(problem.l), dp(problem.u)]
+            kind = MEM_DEVICE
+        else:
+            rp = np.ascontiguousarray(problem.row_ptr, dtype=np.int64)
+            ci = np.ascontiguousarray(problem.col_idx, dtype=np.int32)
+            v = np.ascontiguousarray(problem.val, dtype=np.float64)
+            se = np.ascontiguousarray(problem.sense, dtype=np.int8)
+            self._keep = (rp, ci, v, se, _f64(problem.q, self.m), _f64(problem.c, self.n),
+                          _f64(problem.l, self.n), _f64(problem.u, self.n))
+            nnz = int(rp[-1])
+            args = [_ptr(a) for a in self._keep]
+            kind = MEM_HOST
+        s = L.aapdhg_create(self.m, self.n, nnz, *args, PRECISIONS[precision], kind,
+                            C.c_void_p(stream.cuda_stream), C.byref(self._h))
+        if s != OK:
+            raise AAPDHGError(s, L.aapdhg_last_error(None).decode())
+        self._keep = None
+        self.precision = precision
+
+    # -- helpers -------------------------------------------------------------
+    def _check(self, s, allow=(OK,)):
+        if s not in allow:
+            raise AAPDHGError(s, self._L.aapdhg_last_error(self._h).decode())
+        return s
+
+    def close(self):
+        if self._h:
+            self._L.aapdhg_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- C ABI ---------------------------------------------------------------
+    def set_steps(self, tau, sigma):
+        self._check(self._L.aapdhg_set_steps(self._h, float(tau), float(sigma)))
+
+    def estimate_norm(self, iters=100, seed=1):
+        out = C.c_double()
+        self._check(self._L.aapdhg_estimate_norm(self._h, int(iters), int(seed), C.byref(out)))
+        return out.value
+
+    def set_method(self, method="aa", mem=5, D=10.0, eps=1.0, eta=1e-10, beta=1.0, c_s=0.2,
+                   kappa=1e8, c_div=1.0, dhat_mode=1, faa_adaptive=1):
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        self._check(self._L.aapdhg_set_method(self._h, m, int(mem), D, eps, eta, beta, c_s,
+                                              kappa, c_div, int(dhat_mode), int(faa_adaptive)))
+
+    def set_start(self, x0=None, y0=None):
+        x0 = None if x0 is None else _f64(x0, self.n)
+        y0 = None if y0 is None else _f64(y0, self.m)
+        self._check(self._L.aapdhg_set_start(self._h, _ptr(x0), _ptr(y0)))
+
+    def reset(self):
+        self._check(self._L.aapdhg_reset(self._h))
+
+    def iterate(self, max_iters, tol=0.0, kkt_every=0):
+        done = C.c_int64()
+        s = self._check(self._L.aapdhg_iterate(self._h, int(max_iters), float(tol),
+                                               int(kkt_every), C.byref(done)),
+                        allow=(OK, NOT_CONVERGED))
+        return s == OK, done.value
+
+    def get_iterate(self):
+        x = np.empty(self.n)
+        y = np.empty(self.m)
+        self._check(self._L.aapdhg_get_iterate(self._h, _ptr(x), _ptr(y)))
+        return x, y
+
+    def get_kkt(self):
+        out = np.empty(6)
+        self._check(self._L.aapdhg_get_kkt(self._h, _ptr(out)))
+        return dict(zip(("r_p", "r_d", "r_g", "kkt", "pobj", "dobj"), out.tolist()))
+
+    def counters(self):
+        v = np.zeros(4, dtype=np.int64)
+        p = [C.c_void_p(v.ctypes.data + 8 * k) for k in range(4)]
+        self._check(self._L.aapdhg_get_counters(self._h, *p))
+        return dict(aa_steps=int(v[0]), pdhg_steps=int(v[1]), iters=int(v[2]),
+                    ls_failures=int(v[3]))
+
+    def set_trace(self, capacity):
+        self._check(self._L.aapdhg_set_trace(self._h, int(capacity)))
+        self._trace_cap = int(capacity)
+
+    def get_trace(self):
+        cap = getattr(self, "_trace_cap", 0)
+        n = C.c_int64(cap)
+        br = np.full(cap, -1, np.int8)
+        gn = np.full(cap, np.nan)
+        kk = np.full(cap, np.nan)
+        mk = np.full(cap, -1, np.int32)
+        self._check(self._L.aapdhg_get_trace(self._h, C.byref(n), _ptr(br), _ptr(gn), _ptr(kk),
+                                             _ptr(mk)))
+        k = n.value
+        return dict(branch=br[:k], gnorm=gn[:k], kkt=kk[:k], mk=mk[:k])
+
+    def device_bytes(self):
+        b = C.c_int64()
+        self._check(self._L.aapdhg_device_bytes(self._h, C.byref(b)))
+        return b.value

@@ -1,0 +1,878 @@
+// Host runtime and C ABI of the GB300 AA-PDHG / FAA-PDHG solver.
+//
+// create():  validate the CSR of K = [G; A] (eq. LP-O), renumber rows of K and
+//            of K' longest-first, build both row-sliced CSR copies, the
+//            lanes-per-row segment tables and the split-row chunk tables, move
+//            everything to the device and form D-hat and ||q||, ||c|| there.
+// iterate(): launch the per-iteration kernel sequence in chunks on the
+//            handle's stream; poll the device-side done / error flags once per
+//            chunk.  All branch decisions (termination, safeguard, factorisation
+//            failure, filters) are taken on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/aapdhg.h"
+#include "anderson.cuh"
+#include "common.cuh"
+#include "spmv.cuh"
+
+using namespace aap;
+
+namespace {
+
+aapdhg_alloc_fn g_alloc = nullptr;
+aapdhg_free_fn g_free = nullptr;
+void *g_ctx = nullptr;
+thread_local std::string g_create_err;
+
+constexpr int CHUNK_ITERS = 64;   // iterations launched between two host polls
+constexpr int LPR_ITEMS = 4;      // target entries per lane when choosing lanes per row
+constexpr int LONG_ROW = 32 * 32; // rows longer than this are split into chunks
+
+struct HostCSR {
+    int32_t rows = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double> val;
+};
+
+// Per-matrix device-side tables built on the host.
+struct SegHost {
+    SegTable t{};
+    std::vector<int32_t> chunk_row, row_chunk0;
+};
+
+SegHost build_segments(const HostCSR &A) {
+    SegHost S;
+    S.t.nseg = 0;
+    const int32_t R = A.rows;
+    auto len = [&](int32_t r) { return A.rp[r + 1] - A.rp[r]; };
+    // split rows: rows are sorted longest first, so they form a prefix
+    int32_t nlong = 0;
+    while (nlong < R && len(nlong) > LONG_ROW) ++nlong;
+    S.row_chunk0.assign(nlong + 1, 0);
+    for (int32_t r = 0; r < nlong; ++r) {
+        const int32_t nch = (len(r) + LONG_CHUNK - 1) / LONG_CHUNK;
+        S.row_chunk0[r + 1] = S.row_chunk0[r] + nch;
+        for (int32_t c = 0; c < nch; ++c) S.chunk_row.push_back(r);
+    }
+    S.t.n_long = nlong;
+    S.t.n_chunks = S.row_chunk0[nlong];
+    int64_t tasks = 0;
+    int s = 0;
+    S.t.task0[0] = 0;
+    // segment 0: split rows (present even when empty so lpr 0 is always first)
+    S.t.lpr[s] = 0;
+    S.t.row0[s] = 0;
+    S.t.row1[s] = nlong;
+    tasks += S.t.n_chunks;
+    S.t.task0[++s] = tasks;
+    int32_t r = nlong;
+    for (int lpr = 32; lpr >= 1; lpr >>= 1) {
+        // rows whose length needs lpr lanes: len > (lpr/2) * LPR_ITEMS, or all rest for lpr = 1
+        const int32_t lo_len = (lpr == 1) ? -1 : (lpr / 2) * LPR_ITEMS;
+        const int32_t r0 = r;
+        while (r < R && len(r) > lo_len) ++r;
+        if (r == r0) continue;
+        S.t.lpr[s] = lpr;
+        S.t.row0[s] = r0;
+        S.t.row1[s] = r;
+        const int32_t rpw = 32 / lpr;
+        tasks += (int64_t)((r - r0) + rpw - 1) / rpw;
+        S.t.task0[++s] = tasks;
+    }
+    S.t.nseg = s;
+    return S;
+}
+
+}  // namespace
+
+struct DevAlloc {
+    void *p;
+    size_t bytes;
+};
+
+struct aapdhg_s {
+    int32_t m = 0, n = 0;
+    int64_t nnz = 0, N = 0, Npad = 0;
+    int32_t prec = AAPDHG_MIXED;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, sm_count = 0;
+    aapdhg_status sticky = AAPDHG_OK;
+    std::string err;
+    std::vector<DevAlloc> allocs;
+    int64_t bytes = 0;
+
+    std::vector<int32_t> perm_x, perm_y;   // internal -> caller order
+    std::vector<double> lo_x, hi_x;        // caller order bounds (projection of a start)
+    std::vector<int8_t> sense;             // caller order
+    std::vector<double> x0, y0;            // caller order start (projected)
+
+    Prob<float> pf{};
+    Prob<double> pd{};
+    MethodParams mp{};
+    bool have_steps = false;
+    bool rings_ok = false;
+    int32_t ring_mem = -1;                 // m_A the rings were sized for
+    int32_t grid5 = 1;
+    DevState *st = nullptr;
+    DevState *st_host = nullptr;           // pinned mirror
+    // trace
+    int64_t tr_cap = 0;
+    // raw device pointers kept for re-initialisation
+    void *d_UP = nullptr;
+    void *d_lo = nullptr;
+    void *d_hi = nullptr;
+    // chunk counters to zero at create
+};
+
+namespace {
+
+aapdhg_status fail(aapdhg_t h, aapdhg_status s, const std::string &msg) {
+    if (h) {
+        if (h->sticky == AAPDHG_OK) {
+            h->sticky = s;
+            h->err = msg;
+        }
+    } else {
+        g_create_err = msg;
+    }
+    return s;
+}
+
+#define CK(h, call)                                                                         \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail((h), AAPDHG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *dev_alloc(aapdhg_t h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (g_alloc) {
+        p = g_alloc(bytes, g_ctx);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    if (p) {
+        h->allocs.push_back({p, bytes});
+        h->bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+void dev_free_all(aapdhg_t h) {
+    for (auto &a : h->allocs) {
+        if (g_free) g_free(a.p, g_ctx);
+        else cudaFree(a.p);
+    }
+    h->allocs.clear();
+    h->bytes = 0;
+}
+
+template <typename T>
+T *alloc_copy(aapdhg_t h, const T *src, size_t count, bool *ok) {
+    T *d = (T *)dev_alloc(h, sizeof(T) * count);
+    if (!d) { *ok = false; return nullptr; }
+    if (count && src &&
+        cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
+        *ok = false;
+    }
+    return d;
+}
+
+// Build the internal CSR of K (rows renumbered longest-first, columns mapped
+// to the internal variable order) and of K' (likewise), both with column
+// indices ascending within each row.
+void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                    std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
+                    HostCSR &KT) {
+    std::vector<int64_t> rlen(m), clen(n, 0);
+    for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
+    for (int64_t k = 0; k < rp[m]; ++k) clen[ci[k]]++;
+    perm_y.resize(m);
+    perm_x.resize(n);
+    for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
+    for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
+    std::stable_sort(perm_y.begin(), perm_y.end(), [&](int32_t a, int32_t b) { return rlen[a] > rlen[b]; });
+    std::stable_sort(perm_x.begin(), perm_x.end(), [&](int32_t a, int32_t b) { return clen[a] > clen[b]; });
+    std::vector<int32_t> inv_x(n), inv_y(m);
+    for (int32_t j = 0; j < n; ++j) inv_x[perm_x[j]] = j;
+    for (int32_t i = 0; i < m; ++i) inv_y[perm_y[i]] = i;
+    const int64_t Z = rp[m];
+    // K' rows (internal x) with internal y column indices: counting sort over
+    // internal x while walking internal rows in order -> ascending columns.
+    KT.rows = n;
+    KT.rp.assign(n + 1, 0);
+    for (int32_t j = 0; j < n; ++j) KT.rp[j + 1] = KT.rp[j] + (int32_t)clen[perm_x[j]];
+    KT.ci.resize(Z);
+    KT.val.resize(Z);
+    {
+        std::vector<int32_t> pos(KT.rp.begin(), KT.rp.end() - 1);
+        for (int32_t ii = 0; ii < m; ++ii) {
+            const int32_t i = perm_y[ii];
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t jj = inv_x[ci[k]];
+                const int32_t p = pos[jj]++;
+                KT.ci[p] = ii;
+                KT.val[p] = val[k];
+            }
+        }
+    }
+    // K rows (internal y) with internal x columns, ascending: transpose K'.
+    K.rows = m;
+    K.rp.assign(m + 1, 0);
+    for (int32_t ii = 0; ii < m; ++ii) K.rp[ii + 1] = K.rp[ii] + (int32_t)rlen[perm_y[ii]];
+    K.ci.resize(Z);
+    K.val.resize(Z);
+    {
+        std::vector<int32_t> pos(K.rp.begin(), K.rp.end() - 1);
+        for (int32_t jj = 0; jj < n; ++jj)
+            for (int32_t p = KT.rp[jj]; p < KT.rp[jj + 1]; ++p) {
+                const int32_t ii = KT.ci[p];
+                const int32_t q = pos[ii]++;
+                K.ci[q] = jj;
+                K.val[q] = KT.val[p];
+            }
+    }
+}
+
+// D-hat of the Remark on its construction (mode 1) or the identity (mode 0):
+// per row of K' (a variable) and per row of K (a constraint),
+// sqrt(max(max |entry|, 1e-10)).
+template <typename V>
+__global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mode, V *dh) {
+    const int64_t N = (int64_t)n + m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (mode == 0) { dh[e] = V(1); continue; }
+        const CSRView<V> &A = e < n ? KT : K;
+        const int32_t r = (int32_t)(e < n ? e : e - n);
+        double mx = 0.0;
+        for (int32_t k = A.rp[r]; k < A.rp[r + 1]; ++k) mx = fmax(mx, fabs((double)A.val[k]));
+        dh[e] = (V)sqrt(fmax(mx, 1e-10));
+    }
+}
+
+// ||v||_2^2 of a vector into st->scratch[slot] (last-block finalize).
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_norm2(const V *v, int64_t len, double *part,
+                                                 DevState *st, int slot) {
+    __shared__ double sh[BLOCK];
+    Acc<V> a;
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < len;
+         e += (int64_t)gridDim.x * BLOCK)
+        a.add_sq(v[e]);
+    Acc<V> a1[1] = {a};
+    block_reduce_store<V, 1>(a1, sh, part + blockIdx.x);
+    if (last_block(&st->cnt_norm)) {
+        const double s = block_sum_partials(part, gridDim.x, 1, 0, sh);
+        if (threadIdx.x == 0) st->scratch[slot] = s;
+    }
+}
+
+template <typename V> Prob<V> &prob(aapdhg_t h);
+template <> Prob<float> &prob<float>(aapdhg_t h) { return h->pf; }
+template <> Prob<double> &prob<double>(aapdhg_t h) { return h->pd; }
+
+int grid_for(aapdhg_t h, int64_t blocks_needed, int occ) {
+    const int64_t cap = (int64_t)h->sm_count * std::max(occ, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, cap));
+}
+
+template <typename V>
+aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, const int8_t *sense,
+                           const double *q, const double *c, const double *lb, const double *ub) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = prob<V>(h);
+    const int32_t m = h->m, n = h->n;
+    const int64_t N = h->N, Z = h->nnz;
+    bool ok = true;
+    P.m = m;
+    P.n = n;
+    P.N = N;
+    P.Npad = h->Npad;
+
+    auto to_v = [](const std::vector<double> &a) {
+        std::vector<V> o(a.size());
+        for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
+        return o;
+    };
+    auto mk_csr = [&](const HostCSR &A, CSRView<V> &view, SegHost &sh) {
+        sh = build_segments(A);
+        view.rows = A.rows;
+        view.rp = alloc_copy(h, A.rp.data(), A.rp.size(), &ok);
+        view.ci = alloc_copy(h, A.ci.data(), std::max<size_t>(A.ci.size(), 1), &ok);
+        std::vector<V> v = to_v(A.val);
+        if (v.empty()) v.push_back(V(0));
+        view.val = alloc_copy(h, v.data(), v.size(), &ok);
+        view.seg = sh.t;
+        std::vector<int32_t> cr = sh.chunk_row;
+        if (cr.empty()) cr.push_back(0);
+        view.seg.chunk_row = alloc_copy(h, cr.data(), cr.size(), &ok);
+        view.seg.row_chunk0 = alloc_copy(h, sh.row_chunk0.data(), sh.row_chunk0.size(), &ok);
+        view.chunk_part = (V *)dev_alloc(h, sizeof(V) * 2 * std::max(1, sh.t.n_chunks));
+        view.chunk_cnt = (uint32_t *)dev_alloc(h, sizeof(uint32_t) * std::max(1, sh.t.n_long));
+        if (!view.chunk_part || !view.chunk_cnt) ok = false;
+        else if (cudaMemsetAsync(view.chunk_cnt, 0, sizeof(uint32_t) * std::max(1, sh.t.n_long),
+                                 h->stream) != cudaSuccess) ok = false;
+    };
+    SegHost sT, sK;
+    mk_csr(KT, P.KT, sT);
+    mk_csr(K, P.K, sK);
+    (void)Z;
+
+    // vectors in internal order
+    std::vector<V> cv(n), lov(N), hiv(N), qv(std::max(m, 1));
+    for (int32_t j = 0; j < n; ++j) {
+        const int32_t oj = h->perm_x[j];
+        cv[j] = (V)c[oj];
+        lov[j] = (V)lb[oj];
+        hiv[j] = (V)ub[oj];
+    }
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t oi = h->perm_y[i];
+        qv[i] = (V)q[oi];
+        lov[n + i] = sense[oi] == AAPDHG_ROW_GE ? V(0) : (V)(-INFINITY);
+        hiv[n + i] = (V)INFINITY;
+    }
+    P.c = alloc_copy(h, cv.data(), cv.size(), &ok);
+    P.q = alloc_copy(h, qv.data(), qv.size(), &ok);
+    P.lo = alloc_copy(h, lov.data(), lov.size(), &ok);
+    P.hi = alloc_copy(h, hiv.data(), hiv.size(), &ok);
+    P.UP = (V2 *)dev_alloc(h, sizeof(V2) * N);
+    P.dh = (V *)dev_alloc(h, sizeof(V) * N);
+    P.g = (V *)dev_alloc(h, sizeof(V) * N);
+    if (!P.UP || !P.dh || !P.g) ok = false;
+    h->d_UP = P.UP;
+
+    // fixed grids (deterministic reductions)
+    int occ1 = 0, occ2 = 0, occ3 = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep<V, true>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep<V, true>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, MAXM>, BLOCK, 0);
+    const int64_t tasksT = P.KT.seg.task0[P.KT.seg.nseg], tasksK = P.K.seg.task0[P.K.seg.nseg];
+    P.grid1 = grid_for(h, (tasksT + WARPS - 1) / WARPS, occ1);
+    P.grid2 = grid_for(h, (tasksK + WARPS - 1) / WARPS, occ2);
+    P.grid3 = grid_for(h, (N + BLOCK - 1) / BLOCK, std::max(occ3, 1));
+    h->grid5 = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
+    P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * P.grid1);
+    P.part2 = (double *)dev_alloc(h, sizeof(double) * 3 * P.grid2);
+    P.part3 = (double *)dev_alloc(h, sizeof(double) * (MAXM + 3) * std::max(P.grid3, h->grid5));
+    h->st = (DevState *)dev_alloc(h, sizeof(DevState));
+    P.st = h->st;
+    if (!P.part1 || !P.part2 || !P.part3 || !h->st) ok = false;
+    if (!ok) return fail(h, AAPDHG_ERR_OOM, "device allocation or copy failed during create");
+    CK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+    P.DG = P.W = nullptr;
+    P.tr = Trace{0, nullptr, nullptr, nullptr, nullptr};
+
+    // D-hat and the norms ||q||, ||c|| on the device
+    const int gE = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
+    k_dhat<V><<<gE, BLOCK, 0, h->stream>>>(P.KT, P.K, n, m, 1, const_cast<V *>(P.dh));
+    k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.q, m, P.part3, h->st, 0);
+    k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.c, n, P.part3, h->st, 1);
+    CK(h, cudaGetLastError());
+    CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->mp.q_norm = sqrt(h->st_host->scratch[0]);
+    h->mp.c_norm = sqrt(h->st_host->scratch[1]);
+    return AAPDHG_OK;
+}
+
+// (Re)size the Anderson rings for memory M.
+template <typename V> aapdhg_status ensure_rings(aapdhg_t h, int32_t M) {
+    Prob<V> &P = prob<V>(h);
+    if (M == 0 || (P.DG && h->ring_mem >= M)) return AAPDHG_OK;
+    // rings always hold NSLOT slots: allocate once at full size
+    P.DG = (V *)dev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
+    P.W = (V *)dev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
+    if (!P.DG || !P.W) return fail(h, AAPDHG_ERR_OOM, "device allocation of the Anderson memory failed");
+    h->ring_mem = MAXM;
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status reset_run(aapdhg_t h) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = prob<V>(h);
+    const int32_t n = h->n, m = h->m;
+    std::vector<V2> up(h->N);
+    for (int32_t j = 0; j < n; ++j) {
+        const int32_t oj = h->perm_x[j];
+        up[j].x = (V)h->x0[oj];
+        up[j].y = V(0);
+    }
+    for (int32_t i = 0; i < m; ++i) {
+        const int32_t oi = h->perm_y[i];
+        up[n + i].x = (V)h->y0[oi];
+        up[n + i].y = V(0);
+    }
+    CK(h, cudaMemcpyAsync(P.UP, up.data(), sizeof(V2) * h->N, cudaMemcpyHostToDevice, h->stream));
+    // clear the run fields of the state, keep the norm scratch
+    CK(h, cudaMemsetAsync(h->st, 0, offsetof(DevState, scratch), h->stream));
+    if (P.tr.cap > 0) {
+        std::vector<int8_t> b(P.tr.cap, -1);
+        std::vector<double> nanv(P.tr.cap, NAN);
+        std::vector<int32_t> mk(P.tr.cap, -1);
+        CK(h, cudaMemcpyAsync(P.tr.branch, b.data(), P.tr.cap, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(P.tr.gnorm, nanv.data(), 8 * P.tr.cap, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(P.tr.kkt, nanv.data(), 8 * P.tr.cap, cudaMemcpyHostToDevice, h->stream));
+        CK(h, cudaMemcpyAsync(P.tr.mk, mk.data(), 4 * P.tr.cap, cudaMemcpyHostToDevice, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AAPDHG_OK;
+}
+
+aapdhg_status reset_any(aapdhg_t h) {
+    return h->prec == AAPDHG_FP64 ? reset_run<double>(h) : reset_run<float>(h);
+}
+
+template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode) {
+    Prob<V> &P = prob<V>(h);
+    const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
+    const int g3 = M > 0 ? P.grid3 : 1;
+    k_memory<V, MC><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    if (mode == MODE_ITER && M > 0) k_mix<V, MC><<<h->grid5, BLOCK, 0, h->stream>>>(P, h->mp);
+}
+
+template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
+    Prob<V> &P = prob<V>(h);
+    if (kkt) {
+        k_xstep<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+        k_ystep<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    } else {
+        k_xstep<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+        k_ystep<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    }
+}
+
+template <typename V> void launch_memory_any(aapdhg_t h, int mode) {
+    const int M = h->mp.mem;
+    if (M <= 4) launch_memory_mix<V, 4>(h, mode);
+    else if (M <= 8) launch_memory_mix<V, 8>(h, mode);
+    else if (M <= 16) launch_memory_mix<V, 16>(h, mode);
+    else launch_memory_mix<V, 32>(h, mode);
+}
+
+template <typename V> void launch_iteration(aapdhg_t h, bool kkt, int mode) {
+    launch_T<V>(h, kkt, mode);
+    if (mode != MODE_EVAL) launch_memory_any<V>(h, mode);
+}
+
+aapdhg_status read_state(aapdhg_t h) {
+    CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, double tol,
+                                              int32_t kkt_every, int64_t *done_iters) {
+    Prob<V> &P = prob<V>(h);
+    h->mp.tol = tol;
+    h->mp.kkt_every = kkt_every;
+    aapdhg_status s = ensure_rings<V>(h, (h->mp.method == 0) ? 0 : h->mp.mem);
+    if (s != AAPDHG_OK) return s;
+    if ((s = read_state(h)) != AAPDHG_OK) return s;
+    if (!h->st_host->init_done) {
+        launch_iteration<V>(h, false, MODE_INIT);
+        CK(h, cudaGetLastError());
+        if ((s = read_state(h)) != AAPDHG_OK) return s;
+    }
+    if (h->st_host->error) return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
+    // a new call re-tests the current iterate against its own tolerance
+    CK(h, cudaMemsetAsync(&h->st->done, 0, sizeof(int32_t), h->stream));
+    const int64_t it0 = h->st_host->it;
+    int64_t hit = it0, launched = 0;
+    bool done = false;
+    while (launched < max_iters && !done) {
+        const int64_t chunk = std::min<int64_t>(CHUNK_ITERS, max_iters - launched);
+        for (int64_t c = 0; c < chunk; ++c) {
+            const int64_t itc = hit + c;
+            const bool kkt = kkt_every > 0 && (itc % kkt_every) == 0;
+            launch_iteration<V>(h, kkt, MODE_ITER);
+        }
+        CK(h, cudaGetLastError());
+        launched += chunk;
+        if ((s = read_state(h)) != AAPDHG_OK) return s;
+        if (h->st_host->error) return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
+        done = h->st_host->done != 0;
+        hit = h->st_host->it;
+    }
+    (void)P;
+    if (done_iters) *done_iters = hit - it0;
+    if (done) return AAPDHG_OK;
+    // max_iters may also end exactly on a converged iterate that was not tested
+    return AAPDHG_NOT_CONVERGED;
+}
+
+template <typename V> aapdhg_status get_iterate_t(aapdhg_t h, double *x, double *y) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = prob<V>(h);
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    const int cur = h->st_host->init_done ? (int)((h->st_host->it & 1) ^ 1) : 0;
+    std::vector<V2> up(h->N);
+    CK(h, cudaMemcpyAsync(up.data(), P.UP, sizeof(V2) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    if (x)
+        for (int32_t j = 0; j < h->n; ++j) x[h->perm_x[j]] = (double)(cur ? up[j].y : up[j].x);
+    if (y)
+        for (int32_t i = 0; i < h->m; ++i)
+            y[h->perm_y[i]] = (double)(cur ? up[h->n + i].y : up[h->n + i].x);
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status get_kkt_t(aapdhg_t h, double *out6) {
+    launch_iteration<V>(h, true, MODE_EVAL);
+    CK(h, cudaGetLastError());
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    for (int k = 0; k < 6; ++k) out6[k] = h->st_host->kkt[k];
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status estimate_norm_t(aapdhg_t h, int32_t iters, uint64_t seed,
+                                                   double *norm) {
+    Prob<V> &P = prob<V>(h);
+    const int32_t n = h->n, m = h->m;
+    V *v = (V *)dev_alloc(h, sizeof(V) * n);
+    V *w = (V *)dev_alloc(h, sizeof(V) * std::max(m, 1));
+    double *part = (double *)dev_alloc(h, sizeof(double) * std::max(P.grid1, P.grid2));
+    if (!v || !w || !part) return fail(h, AAPDHG_ERR_OOM, "power iteration buffers");
+    std::vector<V> hv(n);
+    uint64_t z = seed ? seed : 0x9E3779B97F4A7C15ull;
+    for (int32_t j = 0; j < n; ++j) {     // splitmix64 uniform in [-1, 1)
+        z += 0x9E3779B97F4A7C15ull;
+        uint64_t t = z;
+        t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ull;
+        t = (t ^ (t >> 27)) * 0x94D049BB133111EBull;
+        t ^= t >> 31;
+        hv[j] = (V)((double)(t >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+    }
+    CK(h, cudaMemcpyAsync(v, hv.data(), sizeof(V) * n, cudaMemcpyHostToDevice, h->stream));
+    std::vector<double> hp(std::max(P.grid1, P.grid2));
+    double lam = 0.0;
+    for (int32_t t = 0; t < iters; ++t) {
+        if (m > 0) k_spmv_plain<V><<<P.grid2, BLOCK, 0, h->stream>>>(P.K, v, w, part);
+        k_spmv_plain<V><<<P.grid1, BLOCK, 0, h->stream>>>(P.KT, w, v, part);
+        CK(h, cudaGetLastError());
+        CK(h, cudaMemcpyAsync(hp.data(), part, sizeof(double) * P.grid1, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        double s = 0.0;
+        for (int b = 0; b < P.grid1; ++b) s += hp[b];
+        lam = sqrt(s);                   // ||K'K v|| for the unit v of this step
+        k_scale<V><<<grid_for(h, (n + BLOCK - 1) / BLOCK, 4), BLOCK, 0, h->stream>>>(v, n, part, P.grid1);
+        CK(h, cudaGetLastError());
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    // free the scratch (last three allocations)
+    for (int k = 0; k < 3; ++k) {
+        DevAlloc a = h->allocs.back();
+        h->allocs.pop_back();
+        h->bytes -= (int64_t)a.bytes;
+        if (g_free) g_free(a.p, g_ctx); else cudaFree(a.p);
+    }
+    *norm = sqrt(lam);
+    return AAPDHG_OK;
+}
+
+bool finite_all(const double *a, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite(a[i])) return false;
+    return true;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+aapdhg_status aapdhg_set_allocator(aapdhg_alloc_fn alloc, aapdhg_free_fn free_fn, void *ctx) {
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_ctx = ctx;
+    if (!alloc || !free_fn) { g_alloc = nullptr; g_free = nullptr; g_ctx = nullptr; }
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_create(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                            const int32_t *col_idx, const double *val, const int8_t *row_sense,
+                            const double *q, const double *c, const double *lb, const double *ub,
+                            int32_t precision, int32_t mem_kind, void *cuda_stream, aapdhg_t *out) {
+    if (!out) return fail(nullptr, AAPDHG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (m < 0 || n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31))
+        return fail(nullptr, AAPDHG_ERR_INVALID, "need m >= 0, n >= 1, 0 <= nnz < 2^31");
+    if (precision != AAPDHG_FP64 && precision != AAPDHG_MIXED)
+        return fail(nullptr, AAPDHG_ERR_INVALID, "unknown precision");
+    if (mem_kind != AAPDHG_MEM_HOST && mem_kind != AAPDHG_MEM_DEVICE)
+        return fail(nullptr, AAPDHG_ERR_INVALID, "unknown mem_kind");
+    if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || (m > 0 && (!row_sense || !q)) || !c || !lb || !ub)
+        return fail(nullptr, AAPDHG_ERR_INVALID, "NULL input array");
+
+    // Device inputs are brought to the host once: the renumbering below is host work.
+    std::vector<int64_t> rp_h;
+    std::vector<int32_t> ci_h;
+    std::vector<double> val_h, q_h, c_h, lb_h, ub_h;
+    std::vector<int8_t> se_h;
+    if (mem_kind == AAPDHG_MEM_DEVICE) {
+        rp_h.resize(m + 1); ci_h.resize(nnz); val_h.resize(nnz); q_h.resize(m); se_h.resize(m);
+        c_h.resize(n); lb_h.resize(n); ub_h.resize(n);
+        cudaError_t e = cudaSuccess;
+        auto cp = [&](void *dst, const void *src, size_t b) {
+            if (b && e == cudaSuccess) e = cudaMemcpy(dst, src, b, cudaMemcpyDeviceToHost);
+        };
+        cp(rp_h.data(), row_ptr, 8 * (size_t)(m + 1));
+        cp(ci_h.data(), col_idx, 4 * (size_t)nnz);
+        cp(val_h.data(), val, 8 * (size_t)nnz);
+        cp(q_h.data(), q, 8 * (size_t)m);
+        cp(se_h.data(), row_sense, (size_t)m);
+        cp(c_h.data(), c, 8 * (size_t)n);
+        cp(lb_h.data(), lb, 8 * (size_t)n);
+        cp(ub_h.data(), ub, 8 * (size_t)n);
+        if (e != cudaSuccess)
+            return fail(nullptr, AAPDHG_ERR_CUDA, std::string("reading device inputs: ") + cudaGetErrorString(e));
+        row_ptr = rp_h.data(); col_idx = ci_h.data(); val = val_h.data(); q = q_h.data();
+        row_sense = se_h.data(); c = c_h.data(); lb = lb_h.data(); ub = ub_h.data();
+    }
+
+    // ---- validation --------------------------------------------------------
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz)
+        return fail(nullptr, AAPDHG_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[m] must be nnz");
+    {
+        std::vector<int32_t> mark(n, -1);
+        for (int32_t i = 0; i < m; ++i) {
+            if (row_ptr[i + 1] < row_ptr[i])
+                return fail(nullptr, AAPDHG_ERR_INVALID, "row_ptr is not non-decreasing");
+            if (row_sense[i] != AAPDHG_ROW_EQ && row_sense[i] != AAPDHG_ROW_GE)
+                return fail(nullptr, AAPDHG_ERR_INVALID, "row_sense must be 0 (=) or 1 (>=)");
+            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int32_t j = col_idx[k];
+                if (j < 0 || j >= n) return fail(nullptr, AAPDHG_ERR_INVALID, "column index out of range");
+                if (mark[j] == i) return fail(nullptr, AAPDHG_ERR_INVALID, "repeated column within a row");
+                mark[j] = i;
+            }
+        }
+    }
+    if (!finite_all(val, nnz) || !finite_all(q, m) || !finite_all(c, n))
+        return fail(nullptr, AAPDHG_ERR_INVALID, "non-finite value in K, q or c");
+    for (int32_t j = 0; j < n; ++j) {
+        if (std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] > ub[j] || lb[j] == INFINITY ||
+            ub[j] == -INFINITY)
+            return fail(nullptr, AAPDHG_ERR_INVALID, "bounds must satisfy lb <= ub, lb < +inf, ub > -inf");
+    }
+
+    aapdhg_t h = new (std::nothrow) aapdhg_s();
+    if (!h) return fail(nullptr, AAPDHG_ERR_OOM, "host allocation");
+    h->m = m; h->n = n; h->nnz = nnz; h->N = (int64_t)n + m; h->prec = precision;
+    h->Npad = (h->N + 63) & ~(int64_t)63;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+        else { e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking); h->own_stream = true; }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->st_host, sizeof(DevState));
+    if (e != cudaSuccess) {
+        std::string msg = std::string("CUDA setup: ") + cudaGetErrorString(e);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return fail(nullptr, AAPDHG_ERR_CUDA, msg);
+    }
+    h->lo_x.assign(lb, lb + n);
+    h->hi_x.assign(ub, ub + n);
+    h->sense.assign(row_sense, row_sense + m);
+
+    HostCSR K, KT;
+    build_internal(m, n, row_ptr, col_idx, val, h->perm_x, h->perm_y, K, KT);
+    aapdhg_status s = precision == AAPDHG_FP64
+                          ? setup_device<double>(h, K, KT, row_sense, q, c, lb, ub)
+                          : setup_device<float>(h, K, KT, row_sense, q, c, lb, ub);
+    if (s == AAPDHG_OK) {
+        h->mp.method = AAPDHG_AA; h->mp.mem = 5; h->mp.D = 10.0; h->mp.eps = 1.0;
+        h->mp.eta = 1e-10; h->mp.beta = 1.0; h->mp.c_s = 0.2; h->mp.kappa = 1e8; h->mp.c_div = 1.0;
+        h->mp.faa_adaptive = 1;
+        aapdhg_set_start(h, nullptr, nullptr);
+        s = h->sticky;
+    }
+    if (s != AAPDHG_OK) {
+        g_create_err = h->err;
+        aapdhg_destroy(h);
+        return s;
+    }
+    *out = h;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_set_steps(aapdhg_t h, double tau, double sigma) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!(tau > 0) || !(sigma > 0) || !std::isfinite(tau) || !std::isfinite(sigma))
+        return fail(h, AAPDHG_ERR_INVALID, "tau and sigma must be finite and > 0");
+    h->mp.tau = tau;
+    h->mp.sigma = sigma;
+    h->have_steps = true;
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_estimate_norm(aapdhg_t h, int32_t iters, uint64_t seed, double *norm) {
+    if (!h || !norm || iters < 1) return h ? fail(h, AAPDHG_ERR_INVALID, "bad arguments") : AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return h->prec == AAPDHG_FP64 ? estimate_norm_t<double>(h, iters, seed, norm)
+                                  : estimate_norm_t<float>(h, iters, seed, norm);
+}
+
+aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double D, double eps,
+                                double eta, double beta, double c_s, double kappa, double c_div,
+                                int32_t dhat_mode, int32_t faa_adaptive) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (method < 0 || method > 2 || m_A < 0 || m_A > AAPDHG_MAX_MEMORY || !(D > 0) || !(eps > 0) ||
+        !(eta >= 0) || !(beta > 0 && beta <= 1) || !(c_s > 0 && c_s <= 1) || !(kappa > 0) ||
+        !(c_div >= 1) || (dhat_mode != 0 && dhat_mode != 1))
+        return fail(h, AAPDHG_ERR_INVALID, "method parameters out of range");
+    h->mp.method = method; h->mp.mem = m_A; h->mp.D = D; h->mp.eps = eps; h->mp.eta = eta;
+    h->mp.beta = beta; h->mp.c_s = c_s; h->mp.kappa = kappa; h->mp.c_div = c_div;
+    h->mp.faa_adaptive = faa_adaptive ? 1 : 0;
+    // D-hat recomputed on the device for the requested mode
+    const int gE = grid_for(h, (h->N + BLOCK - 1) / BLOCK, 4);
+    if (h->prec == AAPDHG_FP64)
+        k_dhat<double><<<gE, BLOCK, 0, h->stream>>>(h->pd.KT, h->pd.K, h->n, h->m, dhat_mode,
+                                                    const_cast<double *>(h->pd.dh));
+    else
+        k_dhat<float><<<gE, BLOCK, 0, h->stream>>>(h->pf.KT, h->pf.K, h->n, h->m, dhat_mode,
+                                                   const_cast<float *>(h->pf.dh));
+    CK(h, cudaGetLastError());
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_set_start(aapdhg_t h, const double *x0, const double *y0) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    h->x0.assign(h->n, 0.0);
+    h->y0.assign(h->m, 0.0);
+    for (int32_t j = 0; j < h->n; ++j) {
+        double v = x0 ? x0[j] : 0.0;
+        if (!std::isfinite(v)) return fail(h, AAPDHG_ERR_INVALID, "non-finite start");
+        h->x0[j] = std::min(std::max(v, h->lo_x[j]), h->hi_x[j]);
+    }
+    for (int32_t i = 0; i < h->m; ++i) {
+        double v = y0 ? y0[i] : 0.0;
+        if (!std::isfinite(v)) return fail(h, AAPDHG_ERR_INVALID, "non-finite start");
+        if (h->sense[i] == AAPDHG_ROW_GE && v < 0) v = 0;
+        h->y0[i] = v;
+    }
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_reset(aapdhg_t h) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_iterate(aapdhg_t h, int64_t max_iters, double tol, int32_t kkt_every,
+                             int64_t *iters_done) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!h->have_steps) return fail(h, AAPDHG_ERR_INVALID, "step sizes not set");
+    if (max_iters < 0 || std::isnan(tol)) return fail(h, AAPDHG_ERR_INVALID, "bad max_iters or tol");
+    return h->prec == AAPDHG_FP64 ? iterate_t<double>(h, max_iters, tol, kkt_every, iters_done)
+                                  : iterate_t<float>(h, max_iters, tol, kkt_every, iters_done);
+}
+
+aapdhg_status aapdhg_get_iterate(aapdhg_t h, double *x, double *y) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return h->prec == AAPDHG_FP64 ? get_iterate_t<double>(h, x, y) : get_iterate_t<float>(h, x, y);
+}
+
+aapdhg_status aapdhg_get_kkt(aapdhg_t h, double *out6) {
+    if (!h || !out6) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!h->have_steps) return fail(h, AAPDHG_ERR_INVALID, "step sizes not set");
+    return h->prec == AAPDHG_FP64 ? get_kkt_t<double>(h, out6) : get_kkt_t<float>(h, out6);
+}
+
+aapdhg_status aapdhg_get_counters(aapdhg_t h, int64_t *aa_steps, int64_t *pdhg_steps,
+                                  int64_t *iters, int64_t *ls_failures) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    if (aa_steps) *aa_steps = h->st_host->n_aa;
+    if (pdhg_steps) *pdhg_steps = h->st_host->n_pd;
+    if (iters) *iters = h->st_host->it;
+    if (ls_failures) *ls_failures = h->st_host->n_lsfail;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_set_trace(aapdhg_t h, int64_t capacity) {
+    if (!h || capacity < 0) return h ? fail(h, AAPDHG_ERR_INVALID, "capacity < 0") : AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    Trace tr{0, nullptr, nullptr, nullptr, nullptr};
+    if (capacity > 0) {
+        tr.cap = capacity;
+        tr.branch = (int8_t *)dev_alloc(h, capacity);
+        tr.gnorm = (double *)dev_alloc(h, 8 * capacity);
+        tr.kkt = (double *)dev_alloc(h, 8 * capacity);
+        tr.mk = (int32_t *)dev_alloc(h, 4 * capacity);
+        if (!tr.branch || !tr.gnorm || !tr.kkt || !tr.mk) return fail(h, AAPDHG_ERR_OOM, "trace buffers");
+    }
+    h->pf.tr = tr;
+    h->pd.tr = tr;
+    h->tr_cap = capacity;
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double *gnorm, double *kkt,
+                               int32_t *mk) {
+    if (!h || !len) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    const Trace &tr = h->prec == AAPDHG_FP64 ? h->pd.tr : h->pf.tr;
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    int64_t n = std::min<int64_t>(*len, std::min<int64_t>(tr.cap, h->st_host->it + 1));
+    if (n < 0) n = 0;
+    if (n > 0) {
+        if (branch) CK(h, cudaMemcpyAsync(branch, tr.branch, n, cudaMemcpyDeviceToHost, h->stream));
+        if (gnorm) CK(h, cudaMemcpyAsync(gnorm, tr.gnorm, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (kkt) CK(h, cudaMemcpyAsync(kkt, tr.kkt, 8 * n, cudaMemcpyDeviceToHost, h->stream));
+        if (mk) CK(h, cudaMemcpyAsync(mk, tr.mk, 4 * n, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+    }
+    *len = n;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_device_bytes(aapdhg_t h, int64_t *bytes) {
+    if (!h || !bytes) return AAPDHG_ERR_INVALID;
+    *bytes = h->bytes;
+    return AAPDHG_OK;
+}
+
+const char *aapdhg_last_error(aapdhg_t h) {
+    if (!h) return g_create_err.c_str();
+    return h->err.c_str();
+}
+
+void aapdhg_destroy(aapdhg_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    dev_free_all(h);
+    if (h->st_host) cudaFreeHost(h->st_host);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,418 @@
+// Anderson part of AA-PDHG (Alg. 2) and FAA-PDHG (Alg. 3-6).
+//
+// Memory layout: two rings of NSLOT slot-major vectors of length Npad,
+//   DG[s] = dg of column s              (the columns of dG^{k-m_k})
+//   W[s]  = du + beta D-hat dg          (the columns of dU + beta D-hat dG)
+// so the update u_AA = u - H g = u + beta D-hat g - (dU + beta D-hat dG) gamma
+// reads one ring.  The Gram matrix dG'dG is kept by slot and updated by one
+// row per iteration (the incremental update of Sec. 5); <dg_s, g^k> is carried
+// along as <dg_s, g^{k-1}> + <dg_s, dg_new>.
+//
+// Per iteration:
+//   k_memory   (every iteration, Alg. 2 "for j = 1..m_k"): g^k = uh - u,
+//              dg = g^k - g^{k-1}, du = u^k - u^{k-1}; writes the new column;
+//              partial dot products <dg_s, dg> for the kept old columns,
+//              ||dg||^2, <dg, g^k>, ||du||^2.  Its last block updates the Gram
+//              matrix, the column list and, when the safeguard passed, solves
+//              for gamma (Cholesky of dG'dG + eta I; or Reverse, AngleFilter,
+//              LengthFilter, Reverse and the QR solve of Alg. 3 from the Gram).
+//   k_mix      (AA step accepted): u^{k+1} = P(u + beta D-hat g - W gamma),
+//              and du for the next column.  A PDHG step needs no pass: the
+//              roles of the two iterate components swap and du = g^k.
+#pragma once
+#include "common.cuh"
+
+namespace aap {
+
+// ---------------------------------------------------------------------------
+// Dense FP64 routines for k <= 32, one warp, matrices in shared memory
+// (row-major, leading dimension NSLOT).
+// ---------------------------------------------------------------------------
+
+// Cholesky A = L L' in place (lower triangle).  Returns false when a pivot is
+// not positive (or not finite).
+__device__ bool warp_cholesky(double *A, int k) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int j = 0; j < k; ++j) {
+        // pivot (lane 0), then column j below the pivot (lane i handles row i)
+        if (lane == 0) {
+            double d = A[j * NSLOT + j];
+            for (int p = 0; p < j; ++p) d -= A[j * NSLOT + p] * A[j * NSLOT + p];
+            A[j * NSLOT + j] = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
+        }
+        __syncwarp();
+        const double piv = A[j * NSLOT + j];
+        if (!(piv > 0.0)) { ok = false; break; }
+        for (int i = j + 1 + lane; i < k; i += 32) {
+            double s = A[i * NSLOT + j];
+            for (int p = 0; p < j; ++p) s -= A[i * NSLOT + p] * A[j * NSLOT + p];
+            A[i * NSLOT + j] = s / piv;
+        }
+        __syncwarp();
+    }
+    return ok;
+}
+
+// Solve L L' x = b (b overwritten by x), lane 0.
+__device__ void chol_solve_lane0(const double *L, double *b, int k) {
+    if ((threadIdx.x & 31) != 0) return;
+    for (int i = 0; i < k; ++i) {
+        double s = b[i];
+        for (int p = 0; p < i; ++p) s -= L[i * NSLOT + p] * b[p];
+        b[i] = s / L[i * NSLOT + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+        double s = b[i];
+        for (int p = i + 1; p < k; ++p) s -= L[p * NSLOT + i] * b[p];
+        b[i] = s / L[i * NSLOT + i];
+    }
+}
+
+// Shared workspace of the solve.
+struct SolveSmem {
+    double A[NSLOT * NSLOT];
+    double b[NSLOT];
+    double sig[NSLOT];
+    double bnd[NSLOT];
+    double pw[NSLOT + 1];
+    int ord[NSLOT];
+    int alive[NSLOT];
+    int kept[NSLOT];
+    int nk;
+    int ok;
+};
+
+// FAA selection (Alg. 4-6) from the Gram matrix.  Input: list (oldest first,
+// k columns).  Output: sm.kept[0..nk) oldest first.  One warp.
+__device__ void faa_select(const DevState *st, int k, double c_s, double kappa, SolveSmem &sm) {
+    const int lane = threadIdx.x & 31;
+    // Reverse (Alg. 6): newest first
+    for (int t = lane; t < k; t += 32) sm.ord[t] = st->list[k - 1 - t];
+    __syncwarp();
+    for (int idx = lane; idx < k * k; idx += 32) {
+        const int a = idx / k, b = idx % k;
+        sm.A[a * NSLOT + b] = st->G[sm.ord[a] * NSLOT + sm.ord[b]];
+    }
+    __syncwarp();
+    // AngleFilter (Alg. 4): one QR of F (newest first).  |r_ii| comes from the
+    // Cholesky factor of F'F; a column whose distance to the earlier span is
+    // below 1e-7 of its norm is treated as dependent (its row of R is zero).
+    // sigma_i = |r_ii| / ||f_i||; columns 2..k with sigma_i < c_s are removed.
+    for (int j = 0; j < k; ++j) {
+        if (lane == 0) {
+            const double gjj = sm.A[j * NSLOT + j];
+            double d = gjj;
+            for (int p = 0; p < j; ++p) d -= sm.A[p * NSLOT + j] * sm.A[p * NSLOT + j];
+            double rjj = d > 0.0 ? sqrt(d) : 0.0;
+            const double sig = gjj > 0.0 ? rjj / sqrt(gjj) : 0.0;
+            sm.sig[j] = sig;
+            if (!(sig >= 1e-7)) rjj = 0.0;
+            sm.b[j] = rjj;                         // r_jj (0: dependent)
+        }
+        __syncwarp();
+        const double rjj = sm.b[j];
+        // row j of R stored in the upper triangle: R[j][i] for i > j
+        for (int i = j + 1 + lane; i < k; i += 32) {
+            double s = sm.A[j * NSLOT + i];
+            for (int p = 0; p < j; ++p) s -= sm.A[p * NSLOT + j] * sm.A[p * NSLOT + i];
+            sm.A[j * NSLOT + i] = rjj > 0.0 ? s / rjj : 0.0;
+        }
+        if (lane == 0) sm.A[j * NSLOT + j] = rjj;
+        __syncwarp();
+    }
+    // Note: the lower triangle of sm.A still holds F'F entries; the diagonal
+    // was overwritten, so ||f_i||^2 is re-read from the Gram below.
+    if (lane == 0) {
+        int na = 0;
+        for (int i = 0; i < k; ++i)
+            if (i == 0 || !(sm.sig[i] < c_s)) sm.alive[na++] = i;
+        // LengthFilter (Alg. 5) over the surviving columns (newest first):
+        // b_j of Proposition 1.2 from ||f_j||, and e_j = ||du_j||.
+        const double c_t = sqrt(1.0 - c_s * c_s);
+        const double rho2 = ((c_t + c_s) / c_s) * ((c_t + c_s) / c_s);
+        sm.pw[0] = 1.0;
+        for (int e = 1; e <= na; ++e) sm.pw[e] = sm.pw[e - 1] * rho2;   // ((c_t+c_s)/c_s)^(2e)
+        double f2[NSLOT];
+        for (int t = 0; t < na; ++t) {
+            const int sl = sm.ord[sm.alive[t]];
+            f2[t] = st->G[sl * NSLOT + sl];
+        }
+        for (int j = 1; j <= na; ++j) {
+            double bj;
+            if (j == 1) {
+                bj = 1.0 / f2[0];
+            } else {
+                // c_t^2 (c_t+c_s)^{2(j-2)} / (||f_1||^2 c_s^{2(j-2)})
+                double s = c_t * c_t * sm.pw[j - 2] / f2[0];
+                // sum_{i=2}^{j-1} c_t^2 (c_t+c_s)^{2(j-i-1)} / (||f_i||^2 c_s^{2(j-i)})
+                for (int i = 2; i <= j - 1; ++i)
+                    s += c_t * c_t * sm.pw[j - i - 1] / (f2[i - 1] * c_s * c_s);
+                s += 1.0 / f2[j - 1];
+                bj = s / (c_s * c_s);
+            }
+            sm.bnd[j - 1] = bj;
+        }
+        int mbar = 0;
+        for (int kk = na; kk >= 1; --kk) {
+            double se = 0.0, sb = 0.0;
+            for (int j = 0; j < kk; ++j) {
+                se += st->en2[sm.ord[sm.alive[j]]];
+                sb += sm.bnd[j];
+            }
+            if (se * sb <= kappa * kappa) { mbar = kk; break; }
+        }
+        // keep the first mbar (newest) survivors; Reverse back to oldest first
+        for (int t = 0; t < mbar; ++t) sm.kept[t] = sm.ord[sm.alive[mbar - 1 - t]];
+        sm.nk = mbar;
+    }
+    __syncwarp();
+}
+
+// Solve for gamma over columns cols[0..k) (oldest first): Cholesky of the
+// Gram block + eta I.  Writes st->use / st->gamma.  One warp.  Returns ok.
+__device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, SolveSmem &sm) {
+    const int lane = threadIdx.x & 31;
+    for (int idx = lane; idx < k * k; idx += 32) {
+        const int a = idx / k, b = idx % k;
+        sm.A[a * NSLOT + b] = st->G[cols[a] * NSLOT + cols[b]] + (a == b ? eta : 0.0);
+    }
+    for (int t = lane; t < k; t += 32) sm.b[t] = st->rhs[cols[t]];
+    __syncwarp();
+    const bool ok = warp_cholesky(sm.A, k);
+    __syncwarp();
+    if (ok) {
+        chol_solve_lane0(sm.A, sm.b, k);
+        __syncwarp();
+        bool fin = true;
+        for (int t = 0; t < k; ++t) fin = fin && isfinite(sm.b[t]);
+        if (!fin) return false;
+        for (int t = lane; t < k; t += 32) {
+            st->use[t] = cols[t];
+            st->gamma[t] = sm.b[t];
+        }
+        if (lane == 0) st->use_count = k;
+    }
+    return ok;
+}
+
+// ---------------------------------------------------------------------------
+// k_memory: the per-iteration memory pass.  MC >= m_A bounds the number of
+// old columns read (compile-time, so the partial sums stay in registers).
+// mode INIT: only g^0 = u^1 - u^0 is written.
+// ---------------------------------------------------------------------------
+template <typename V, int MC>
+__global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, int mode) {
+    DevState *st = P.st;
+    if (st->done | st->error) return;
+    const int M = (mp.method == 0) ? 0 : mp.mem;
+    __shared__ int s_old[NSLOT];
+    __shared__ int s_nold, s_new, s_prev_acc;
+    __shared__ double sh[WARPS * (MC + 3)];
+    const int cur = (mode == MODE_INIT) ? 0 : (int)(st->it & 1) ^ 1;
+
+    if (mode == MODE_INIT) {
+        if (M > 0) {
+            for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
+                 e += (int64_t)gridDim.x * BLOCK) {
+                const typename Vec2<V>::T pr = P.UP[e];
+                P.g[e] = comp<V>(pr, 1 - cur) - comp<V>(pr, cur);
+            }
+        }
+        if (last_block(&st->cnt_ring) && threadIdx.x == 0) {
+            st->count = 0;
+            st->new_slot = 0;
+            st->free_slot = 0;
+            st->accept = 0;   // u^1 = T u^0 behaves as a PDHG step: du^0 = g^0
+            st->use_count = 0;
+            st->it = 0;
+            st->init_done = 1;
+        }
+        return;
+    }
+
+    if (threadIdx.x == 0) {
+        // old columns that stay in the memory after the new one is appended
+        const int cnt = st->count;
+        const int drop = (M > 0 && cnt == M) ? 1 : 0;
+        int t = 0;
+        for (int i = drop; i < cnt; ++i) s_old[t++] = st->list[i];
+        s_nold = t;
+        s_new = st->free_slot;
+        s_prev_acc = st->accept;
+    }
+    __syncthreads();
+    const int nold = s_nold, sn = s_new;
+    const bool prev_acc = s_prev_acc != 0;
+
+    Acc<V> acc[MC + 3];   // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2
+    if (M > 0) {
+        V *DGn = P.DG + (int64_t)sn * P.Npad;
+        V *Wn = P.W + (int64_t)sn * P.Npad;
+        const V beta = (V)mp.beta;
+        for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
+             e += (int64_t)gridDim.x * BLOCK) {
+            const typename Vec2<V>::T pr = P.UP[e];
+            const V u = comp<V>(pr, cur), uh = comp<V>(pr, 1 - cur);
+            const V g = uh - u;
+            const V gp = P.g[e];
+            const V dg = g - gp;
+            const V du = prev_acc ? Wn[e] : gp;     // u^k - u^{k-1}
+            P.g[e] = g;
+            DGn[e] = dg;
+            Wn[e] = du + beta * __ldg(P.dh + e) * dg;
+#pragma unroll
+            for (int s = 0; s < MC; ++s)
+                if (s < nold) acc[s].add_prod(__ldcs(P.DG + (int64_t)s_old[s] * P.Npad + e), dg);
+            acc[MC].add_sq(dg);
+            acc[MC + 1].add_prod(dg, g);
+            acc[MC + 2].add_sq(du);
+        }
+        // block reduce -> partials
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int s = 0; s < MC + 3; ++s) {
+            if (s < nold || s >= MC) {
+                acc[s].warp_allreduce();
+                if (lane == 0) sh[warp * (MC + 3) + s] = acc[s].value();
+            }
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < MC + 3; s += BLOCK) {
+            if (s < nold || s >= MC) {
+                double v = 0.0;
+                for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 3) + s];
+                P.part3[(int64_t)blockIdx.x * (MC + 3) + s] = v;
+            }
+        }
+    }
+    if (!last_block(&st->cnt_ring)) return;
+
+    // ---- final reduction and the m x m work (one block) -------------------
+    __shared__ double red[MC + 3];
+    __shared__ double shs[BLOCK];
+    __shared__ SolveSmem sm;
+    if (M > 0) {
+        for (int s = 0; s < MC + 3; ++s) {
+            if (s < nold || s >= MC) {
+                const double v = block_sum_partials(P.part3, P.grid3, MC + 3, s, shs);
+                if (threadIdx.x == 0) red[s] = v;
+            }
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int accept = 0, lsfail = 0;
+    if (M > 0) {
+        if (lane == 0) {
+            // Gram row / column of the new slot; incremental right-hand side
+            for (int t = 0; t < nold; ++t) {
+                const int s = s_old[t];
+                st->G[s * NSLOT + sn] = red[t];
+                st->G[sn * NSLOT + s] = red[t];
+                st->rhs[s] += red[t];
+            }
+            st->G[sn * NSLOT + sn] = red[MC];
+            st->rhs[sn] = red[MC + 1];
+            st->en2[sn] = red[MC + 2];
+            // list: keep the nold survivors, append the new column
+            for (int t = 0; t < nold; ++t) st->list[t] = s_old[t];
+            st->list[nold] = sn;
+            st->count = nold + 1;
+            st->new_slot = sn;
+        }
+        __syncwarp();
+        if (st->want_aa) {
+            const int k = st->count;
+            if (mp.method == 1) {
+                sm.nk = k;
+                for (int t = lane; t < k; t += 32) sm.kept[t] = st->list[t];
+                __syncwarp();
+                const bool ok = gram_solve(st, sm.kept, k, mp.eta, sm);
+                accept = ok ? 1 : 0;
+                lsfail = ok ? 0 : 1;
+            } else {
+                faa_select(st, k, mp.c_s, mp.kappa, sm);
+                const int nk = sm.nk;
+                bool ok = true;
+                if (nk > 0) ok = gram_solve(st, sm.kept, nk, 0.0, sm);
+                else if (lane == 0) st->use_count = 0;
+                __syncwarp();
+                accept = ok ? 1 : 0;
+                lsfail = ok ? 0 : 1;
+                if (ok && mp.faa_adaptive && lane == 0) {
+                    for (int t = 0; t < nk; ++t) st->list[t] = sm.kept[t];
+                    st->count = nk;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            // slot for the next column's du: any slot not in the list
+            int fs = 0;
+            for (int cand = 0; cand < NSLOT; ++cand) {
+                bool used = false;
+                for (int t = 0; t < st->count; ++t) used = used || (st->list[t] == cand);
+                if (!used) { fs = cand; break; }
+            }
+            st->free_slot = fs;
+        }
+    }
+    if (lane == 0) {
+        const int64_t it = st->it;
+        st->accept = accept;
+        if (accept) st->n_aa += 1; else st->n_pd += 1;
+        if (lsfail) st->n_lsfail += 1;
+        if (it < P.tr.cap) {
+            P.tr.branch[it] = (int8_t)(accept ? 1 : (lsfail ? 2 : 0));
+            P.tr.mk[it] = accept ? st->use_count : -1;
+        }
+        st->it = it + 1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_mix: u^{k+1} = P(u^k + beta D-hat g^k - sum_t gamma_t W[use_t]) written
+// over T(u^k), and du = u^{k+1} - u^k into the free slot (Alg. 2, the AA
+// branch; the projection P of Sec. 3 is a clamp to [lo, hi]).
+// ---------------------------------------------------------------------------
+template <typename V, int MC>
+__global__ void __launch_bounds__(BLOCK) k_mix(Prob<V> P, MethodParams mp) {
+    DevState *st = P.st;
+    if (st->done | st->error) return;
+    if (!st->accept) return;
+    __shared__ V s_gam[MC];
+    __shared__ int s_use[MC];
+    __shared__ int s_k, s_free;
+    if (threadIdx.x == 0) {
+        s_k = st->use_count;
+        s_free = st->free_slot;
+    }
+    if (threadIdx.x < MC) {
+        s_gam[threadIdx.x] = (threadIdx.x < st->use_count) ? (V)st->gamma[threadIdx.x] : V(0);
+        s_use[threadIdx.x] = (threadIdx.x < st->use_count) ? st->use[threadIdx.x] : 0;
+    }
+    __syncthreads();
+    const int k = s_k;
+    // the iteration counter was already advanced by k_memory
+    const int cur = (int)(st->it & 1);
+    const V beta = (V)mp.beta;
+    V *Wf = P.W + (int64_t)s_free * P.Npad;
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
+         e += (int64_t)gridDim.x * BLOCK) {
+        typename Vec2<V>::T pr = P.UP[e];
+        const V u = comp<V>(pr, cur), uh = comp<V>(pr, 1 - cur);
+        V v = u + beta * __ldg(P.dh + e) * (uh - u);
+#pragma unroll
+        for (int t = 0; t < MC; ++t)
+            if (t < k) v = fma(-s_gam[t], __ldcs(P.W + (int64_t)s_use[t] * P.Npad + e), v);
+        const V l = __ldg(P.lo + e), h = __ldg(P.hi + e);
+        v = v < l ? l : (v > h ? h : v);
+        if (cur) pr.x = v; else pr.y = v;
+        P.UP[e] = pr;
+        Wf[e] = v - u;
+    }
+}
+
+}  // namespace aap

@@ -1,0 +1,231 @@
+// Shared device definitions of the AA-PDHG / FAA-PDHG CUDA path (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace aap {
+
+constexpr int MAXM = 32;            // largest Anderson memory m_A
+constexpr int NSLOT = MAXM + 1;     // ring slots: m_A columns + one slot for the next du
+constexpr int BLOCK = 256;          // threads per block of the streaming kernels
+constexpr int WARPS = BLOCK / 32;
+constexpr int LONG_CHUNK = 1024;    // nnz per warp task of a split (long) row
+constexpr int MAX_SEG = 8;          // long-row segment + lanes-per-row 32,16,8,4,2,1
+
+// ---------------------------------------------------------------------------
+// Accumulators.  FP64 mode: plain double.  Mixed mode: a float pair (hi, lo)
+// fed with error-free transformations (exact product via fma, TwoSum), so a
+// per-thread / per-warp partial carries about 44 significant bits, i.e. the
+// accuracy of an FP64 accumulator over the same terms, while every operation
+// runs on the FP32 pipes (the FP64 rate of this part is 1/64 of FP32).  The
+// pair is rounded into a double once per warp and summed in FP64 from there.
+// ---------------------------------------------------------------------------
+template <typename V> struct Acc;
+
+template <> struct Acc<double> {
+    double s;
+    __device__ __forceinline__ Acc() : s(0.0) {}
+    __device__ __forceinline__ void add(double a) { s += a; }
+    __device__ __forceinline__ void add_prod(double a, double b) { s = fma(a, b, s); }
+    __device__ __forceinline__ void add_sq(double a) { s = fma(a, a, s); }
+    __device__ __forceinline__ void warp_allreduce() {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    __device__ __forceinline__ double value() const { return s; }
+};
+
+template <> struct Acc<float> {
+    float hi, lo;
+    __device__ __forceinline__ Acc() : hi(0.f), lo(0.f) {}
+    // TwoSum: hi + a = s + e exactly
+    __device__ __forceinline__ void add(float a) {
+        float s = __fadd_rn(hi, a);
+        float bb = __fsub_rn(s, hi);
+        float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(a, bb));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        float p = __fmul_rn(a, b);
+        float e = __fmaf_rn(a, b, -p);      // a*b = p + e exactly
+        add(p);
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add_sq(float a) { add_prod(a, a); }
+    __device__ __forceinline__ void warp_allreduce() {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+            float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+            add(h2);
+            lo = __fadd_rn(lo, l2);
+        }
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+template <typename V> struct Vec2;
+template <> struct Vec2<float> { typedef float2 T; };
+template <> struct Vec2<double> { typedef double2 T; };
+
+// ---------------------------------------------------------------------------
+// Device-resident run state.  Written only by the single block that finishes
+// a reduction (last-block pattern) and read by the streaming kernels.
+// ---------------------------------------------------------------------------
+struct DevState {
+    int64_t it;            // loop iterations done
+    int64_t n_aa, n_pd;    // i^k, j^k of Alg. 2
+    int64_t n_lsfail;      // AA steps rejected by a failed factorisation
+    int32_t done;          // KKT <= tol reached at the current iterate
+    int32_t error;         // non-zero: NaN/Inf met (iterate left unchanged)
+    int32_t want_aa;       // safeguard passed this iteration
+    int32_t accept;        // AA step taken this iteration
+    int32_t count;         // columns in the memory
+    int32_t new_slot;      // slot receiving the column of this iteration
+    int32_t free_slot;     // slot receiving u^{k+1} - u^k (next column's du)
+    int32_t use_count;     // columns used by the accepted AA step
+    int32_t list[NSLOT];   // memory columns, oldest first
+    int32_t use[NSLOT];    // columns used by the step (slot ids, oldest first)
+    double gamma[NSLOT];   // coefficient of used column t (parallel to use[])
+    double G[NSLOT * NSLOT];  // Gram entries <dg_a, dg_b> by slot
+    double rhs[NSLOT];     // <dg_s, g^k> by slot
+    double en2[NSLOT];     // ||du_s||^2 by slot
+    double g0;             // ||g^0||
+    double gnorm;          // ||g^k||
+    double kkt[6];         // r_p, r_d, r_g, KKT, c'x, dual objective at u^k
+    int32_t kkt_valid;
+    int32_t init_done;     // u^1 = T u^0 and g^0 formed
+    uint32_t cnt_spmv;     // last-block counter of the y-step
+    uint32_t cnt_ring;     // last-block counter of the memory pass
+    uint32_t cnt_norm;     // last-block counter of the norm kernels
+    double scratch[8];
+};
+
+// Method parameters (by value into the kernels).
+struct MethodParams {
+    int32_t method;        // 0 PDHG, 1 AA, 2 FAA
+    int32_t mem;           // m_A
+    double tau, sigma;
+    double D, eps, eta, beta, c_s, kappa, c_div;
+    int32_t faa_adaptive;
+    double tol;
+    int32_t kkt_every;
+    double q_norm, c_norm; // ||q||_2, ||c||_2 (Remark on termination)
+};
+
+// Trace buffers (device); cap = 0 disables.
+struct Trace {
+    int64_t cap;
+    int8_t *branch;
+    double *gnorm;
+    double *kkt;
+    int32_t *mk;
+};
+
+// Lanes-per-row segments of one CSR matrix whose rows are sorted by length,
+// longest first.  Segment 0 holds the split rows (lpr == 0): each is cut
+// into LONG_CHUNK-sized chunks, one warp task per chunk.
+struct SegTable {
+    int32_t nseg;
+    int32_t lpr[MAX_SEG];
+    int32_t row0[MAX_SEG], row1[MAX_SEG];
+    int64_t task0[MAX_SEG + 1];   // prefix sums of warp tasks
+    int32_t n_long;               // split rows (rows [0, n_long))
+    int32_t n_chunks;
+    const int32_t *chunk_row;     // chunk -> row
+    const int32_t *row_chunk0;    // split row -> first chunk (n_long + 1 entries)
+};
+
+template <typename V> struct CSRView {
+    int32_t rows;
+    const int32_t *rp;
+    const int32_t *ci;
+    const V *val;
+    SegTable seg;
+    V *chunk_part;                // n_chunks * 2 partial sums of split rows
+    uint32_t *chunk_cnt;          // n_long arrival counters (self-resetting)
+};
+
+// Everything a kernel needs about the problem and the iterate buffers.
+template <typename V> struct Prob {
+    typedef typename Vec2<V>::T V2;
+    int32_t m, n;
+    int64_t N, Npad;
+    CSRView<V> KT;                // rows = variables (internal order), cols = rows of K
+    CSRView<V> K;                 // rows = constraints (internal order)
+    V2 *UP;                       // (u-hat, u) pairs, x part [0, n), y part [n, N)
+    const V *c;                   // n
+    const V *q;                   // m
+    const V *lo, *hi;             // N: bounds of X, and (0 or -inf, +inf) for Y
+    const V *dh;                  // N: D-hat
+    V *g;                         // N: g^{k-1} / g^k
+    V *DG, *W;                    // NSLOT * Npad rings: dg and du + beta D dg
+    double *part1, *part2, *part3;// block partials of the x-step, y-step, memory pass
+    int32_t grid1, grid2, grid3;  // grids of those kernels (fixed: deterministic sums)
+    DevState *st;
+    Trace tr;
+};
+
+// Iterate storage: UP[e] = (comp0, comp1); comp[cur] is u^k, comp[1 - cur]
+// receives T(u^k).  The roles swap every iteration, so a PDHG step never copies.
+template <typename V>
+__device__ __forceinline__ V comp(const typename Vec2<V>::T &p, int c) { return c ? p.y : p.x; }
+
+// Kernel modes: forming u^1 = T u^0 and g^0, a loop iteration, or a KKT
+// evaluation of the current iterate that changes no run state.
+enum { MODE_INIT = 0, MODE_ITER = 1, MODE_EVAL = 2 };
+
+// Block-wide sum of NV per-thread accumulators into FP64 (fixed order),
+// written to out[0..NV) by thread 0 of the block.  `sh` holds WARPS * NV doubles.
+template <typename V, int NV>
+__device__ __forceinline__ void block_reduce_store(Acc<V> (&acc)[NV], double *sh, double *out) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        acc[k].warp_allreduce();
+        if (lane == 0) sh[warp * NV + k] = acc[k].value();
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double s = 0.0;
+        for (int w = 0; w < WARPS; ++w) s += sh[w * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+}
+
+// Last-block detection: every block calls after writing its partial; returns
+// true in exactly one block (the last to arrive), which then owns the final
+// reduction.  The counter resets itself.
+__device__ __forceinline__ bool last_block(uint32_t *cnt) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t prev = atomicAdd(cnt, 1u);
+        is_last = (prev == gridDim.x - 1);
+        if (is_last) *cnt = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// Fixed-order FP64 sum over `nb` blocks of column k of part[nb][stride], by
+// one block (all threads), result broadcast through shared memory.
+__device__ __forceinline__ double block_sum_partials(const double *part, int nb, int stride,
+                                                     int k, double *sh) {
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += __ldcg(part + (int64_t)b * stride + k);
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+}  // namespace aap

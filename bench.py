@@ -1,0 +1,399 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 AA-PDHG hot path; prints ONE JSON line.
+
+A step is one AA-PDHG loop iteration (Alg. 2): x-step and y-step of T with the
+fused KKT / residual epilogues, the memory pass with the incremental Gram row,
+the safeguard and the m x m solve, and the AA mix with projection.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large|medium|tiny]
+  python bench.py --impl reference ...   (the FP64 CPU oracle as the reference arm)
+
+value      iterations/s of the whole job (sum over ranks; replicas: one LP per
+           rank, no data-path collective), inputs resident in HBM.
+e2e        the same metric through the public API from pinned host buffers:
+           create (host CSR -> device), power-iteration step size, K
+           iterations, read back x and y; per-step bytes = session bytes / K.
+roofline   the dominant kernel (CUDA events on the solver's stream) against
+           the measured HBM copy bandwidth.
+cpu_baseline  the FP64 CPU oracle on a bounded sample of the same LP.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time-to-1e-4 KKT & iters/s vs plain PDHG on 1 GB300; SpMV HBM GB/s; p99 latency"
+UNIT = "iters/s"
+FALLBACK_HBM_GBS = 6800.0
+
+WORKLOADS = {
+    "large": dict(method="aa", mem=20, precision="mixed",
+                  desc="2M x 5M CSR, ~50M nnz, Chung-Lu power-law row/col degrees (exponent "
+                       "2.1), N(0,1)*lognormal(0,3) per row, 20% '>=' rows, bounds [0,U(1,100)] "
+                       "with 10% free; AA-PDHG m=20, FP32 SpMV/iterates + FP64-accurate "
+                       "Gram/solve/safeguard/KKT"),
+    "medium": dict(method="aa", mem=10, precision="mixed",
+                   desc="100k x 300k CSR, ~2M nnz, log-normal row lengths (median 7, max 2000), "
+                        "N(0,1)*lognormal(0,2) per row, 70/30 '='/'>=' rows, bounds [0,U(1,100)] "
+                        "with 10% free; AA-PDHG m=10, mixed precision"),
+    "tiny": dict(method="aa", mem=5, precision="fp64",
+                 desc="200 x 500 CSR, 10 nnz/row, N(0,1), '=' rows, 0<=x<=10; AA-PDHG m=5, FP64"),
+}
+
+
+# ---------------------------------------------------------------------------
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def make_problem(workload, rank, scale=1.0):
+    import lpgen
+    seed = lpgen.SEED_BASE + {"tiny": 1, "medium": 2, "large": 3}[workload] + 1000 * rank
+    if scale != 1.0 and workload == "large":
+        return lpgen.large(seed=seed, m=int(2_000_000 * scale), n=int(5_000_000 * scale),
+                           z=int(50_000_000 * scale))
+    if scale != 1.0 and workload == "medium":
+        return lpgen.medium(seed=seed, m=int(100_000 * scale), n=int(300_000 * scale))
+    return lpgen.WORKLOADS[workload](seed=seed)
+
+
+def problem_bytes(P):
+    return int(8 * (P.m + 1) + 12 * P.nnz + P.m + 8 * (P.m + 3 * P.n))
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev_id):
+        self.dev_id = dev_id
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                                "sw_power_cap"), f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_bytes(P, s_v, kind, M, iters, accepted, use_sum, prev_acc):
+    """Algorithmic HBM bytes of `iters` launches of a kernel kind (see the design
+    notes for the per-unit figures): CSR values + int32 indices + row pointers,
+    compulsory gathers once, every vector read or written once."""
+    n, m, Z = P.n, P.m, P.nnz
+    N = n + m
+    if kind == "xstep":
+        return iters * (Z * (s_v + 4) + 4 * (n + 1) + s_v * m + 7 * s_v * n)
+    if kind == "ystep":
+        return iters * (Z * (s_v + 4) + 4 * (m + 1) + 2 * s_v * n + 6 * s_v * m)
+    if kind == "memory":
+        nold = max(M - 1, 0)
+        return (iters * N * s_v * (7 + nold) + prev_acc * N * s_v) if M > 0 else 0
+    if kind == "mix":
+        return accepted * N * s_v * 8 + use_sum * N * s_v
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_08062_gb300 import Solver
+
+    wl = WORKLOADS[args.workload]
+    P = make_problem(args.workload, rank, args.scale)
+    s_v = 4 if wl["precision"] == "mixed" else 8
+    M = wl["mem"]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    s = Solver(P, precision=wl["precision"], stream=stream)
+    nrm = s.estimate_norm(100, seed=1)
+    tau = sig = 0.9 / nrm
+    s.set_steps(tau, sig)
+    s.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
+    kkt_every = 64
+
+    # warm-up
+    s.iterate(args.warmup, tol=0.0, kkt_every=kkt_every)
+    c0 = s.counters()
+    l0 = s.launch_count()
+    barrier()
+    dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
+    dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_id) as clk:
+        ev0.record(stream)
+        s.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = s.launch_count() - l0
+    c1 = s.counters()
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps / (t_max / 1e3)
+
+    # per-kernel CUDA-event pass (same loop, instrumented), for the roofline
+    s.profile_kernels(True)
+    cp0 = s.counters()
+    s.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+    cp1 = s.counters()
+    prof = s.kernel_profile()
+    s.profile_kernels(False)
+    acc_p = cp1["aa_steps"] - cp0["aa_steps"]
+    it_p = cp1["iters"] - cp0["iters"]
+    kern = {}
+    peak, peak_src = measured_peak()
+    for kind, d in prof.items():
+        if not d["launches"]:
+            continue
+        b = kernel_bytes(P, s_v, kind, M, d["launches"], acc_p, acc_p * M, acc_p)
+        gbs = b / (d["total_ms"] / 1e3) / 1e9 if d["total_ms"] > 0 else None
+        kern[kind] = dict(launches=d["launches"], avg_us=1e3 * d["total_ms"] / d["launches"],
+                          share=None, alg_bytes_per_launch=b / d["launches"], gbs=gbs,
+                          frac_of_measured_hbm=(gbs / peak) if gbs else None)
+    tot = sum(d["total_ms"] for d in prof.values())
+    for kind in kern:
+        kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
+    dom = max(kern, key=lambda k: prof[k]["total_ms"])
+    traffic = None
+    try:
+        tf = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        ent = tf.get(args.workload, {}).get(dom)
+        if ent and ent.get("kernel_sources") == kernel_source_hash():
+            traffic = ent["dram_bytes_per_launch"]
+    except Exception:
+        pass
+    roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["frac_of_measured_hbm"], "traffic": traffic,
+                "kernel": dom, "peak_source": peak_src,
+                "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"]}
+
+    # plain PDHG on the same GPU, same precision
+    s.set_method("pdhg", mem=0)
+    s.iterate(args.warmup, tol=0.0, kkt_every=kkt_every)
+    barrier()
+    ev0.record(stream)
+    s.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+    ev1.record(stream)
+    barrier()
+    pd_ms = ev0.elapsed_time(ev1)
+    kk = s.get_kkt()
+    s.close()
+
+    # end to end through the public API from pinned host buffers
+    import lpgen
+    pin = {}
+    for name in ("row_ptr", "col_idx", "val", "sense", "q", "c", "l", "u"):
+        a = np.ascontiguousarray(getattr(P, name))
+        t = torch.empty(a.shape, dtype=getattr(torch, str(a.dtype)), pin_memory=True)
+        t.numpy()[...] = a
+        pin[name] = t.numpy()
+    Pp = lpgen.Problem(P.m, P.n, **pin)
+    barrier()
+    t0 = time.perf_counter()
+    with Solver(Pp, precision=wl["precision"], stream=stream) as s2:
+        nrm2 = s2.estimate_norm(100, seed=1)
+        s2.set_steps(0.9 / nrm2, 0.9 / nrm2)
+        s2.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
+        s2.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+        x, y = s2.get_iterate()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    polls = (args.steps + 63) // 64 + 2
+    e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": problem_bytes(P) / args.steps,
+           "d2h_bytes_per_step": (8 * (P.n + P.m) + 56 * polls) / args.steps,
+           "session": "create from pinned host CSR (validation, renumbering, H2D) + 100 "
+                      "power iterations + K iterations + x,y read back"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(P, wl, tau, sig, args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if wl["precision"] == "mixed" else "f64",
+            "data": "synthetic (seeded generator, known optimum; one LP per rank)",
+            "config": {"workload": args.workload, "desc": wl["desc"], "m": P.m, "n": P.n,
+                       "nnz": P.nnz, "scale": args.scale, "memory": M, "method": wl["method"],
+                       "precision": wl["precision"], "kkt_every": kkt_every,
+                       "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (no flush)" if P.nnz * 16 > 129e6 else
+                             "inputs fit in L2 (not flushed: back-to-back iterations)"},
+            "roofline": roofline, "kernels": kern,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+            "aa_steps": c1["aa_steps"] - c0["aa_steps"],
+            "plain_pdhg": {"iters_per_s": args.steps / (pd_ms / 1e3), "ms_per_iter": pd_ms / args.steps},
+            "kkt_after_run": kk["kkt"],
+            "time_to_1e-4_s": None,
+            "p99_latency": None,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_2508_08062_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def cpu_baseline(P, wl, tau, sig, workload, budget_s=20.0):
+    """The FP64 oracle as it stands, single-threaded, on the same LP: S AA-PDHG
+    iterations timed end to end (including its one initial T application)."""
+    from oracle import oracle as O
+    lp = O.OracleLP.from_problem(P)
+    prm = O.Params(method={"aa": 1, "faa": 2, "pdhg": 0}[wl["method"]], mem=wl["mem"], tau=tau,
+                   sigma=sig, D=10.0, eps=1.0)
+    t0 = time.perf_counter()
+    O.solve(lp, prm, 1)
+    t1 = time.perf_counter() - t0
+    S = int(max(2, min(1000, budget_s / max(t1, 1e-6))))
+    t0 = time.perf_counter()
+    O.solve(lp, prm, S)
+    ts = time.perf_counter() - t0
+    return {"value": S / ts, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{S} FP64 oracle iterations ({wl['method']}, m={wl['mem']}) on the same "
+                      f"{workload} LP from its start (includes the initial T), 1 thread"}
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    P = make_problem(args.workload, 0, args.scale)
+    from scipy.sparse.linalg import svds
+    import scipy.sparse as sp
+    K = sp.csr_matrix((P.val, P.col_idx.astype(np.int64), P.row_ptr), shape=(P.m, P.n))
+    nrm = svds(K, k=1, return_singular_vectors=False, random_state=0, maxiter=200, tol=1e-3)[0] \
+        if min(P.m, P.n) > 2 else np.linalg.norm(K.toarray(), 2)
+    tau = sig = 0.9 / nrm
+    budget = float(os.environ.get("REF_BUDGET_S", "120"))
+    cb = cpu_baseline(P, wl, tau, sig, args.workload, budget_s=budget)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+            "n_gpus": world, "steps": int(cb["sample"].split()[0]), "warmup": 0,
+            "requested_steps": args.steps, "requested_warmup": args.warmup,
+            "ms_per_step": 1e3 / cb["value"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "m": P.m, "n": P.n,
+                       "nnz": P.nnz, "memory": wl["mem"], "method": wl["method"]},
+            "cpu_baseline": cb,
+            "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink the workload's m, n, nnz (profiling captures only)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

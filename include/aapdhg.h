@@ -169,6 +169,18 @@ aapdhg_status aapdhg_set_trace(aapdhg_t h, int64_t capacity);
 aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double *gnorm,
                                double *kkt, int32_t *mk);
 
+/* Kernel instrumentation for benchmarks.  aapdhg_profile_kernels(h, 1) makes
+ * aapdhg_iterate bracket every kernel it launches with CUDA events recorded on
+ * the handle's stream and accumulate the elapsed times per kernel kind; it
+ * resets the totals (0 turns the events off).  aapdhg_get_kernel_profile
+ * returns, for kind 0 (x-step over K'), 1 (y-step over K), 2 (memory pass and
+ * m x m solve) or 3 (AA mix), the launches and total milliseconds since the
+ * last reset; kind -1 returns the number of kernels aapdhg_iterate launched
+ * since create (counted with or without events) and 0 ms.                    */
+aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable);
+aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
+                                        double *total_ms);
+
 /* Bytes of device memory held by the handle.                                 */
 aapdhg_status aapdhg_device_bytes(aapdhg_t h, int64_t *bytes);
 

@@ -210,16 +210,19 @@ def _power_law_weights(k, exponent, total):
     return w * (total / w.sum())
 
 
-def large(seed=SEED_BASE + 3, m=2_000_000, n=5_000_000, z=50_000_000, exponent=2.1) -> Problem:
+def large(seed=SEED_BASE + 3, m=2_000_000, n=5_000_000, z=50_000_000, exponent=2.1,
+          oversample=1.19) -> Problem:
     """2M x 5M, Chung-Lu power-law degrees, Z about 50M (see module docstring).
 
-    Edges are drawn as z independent (row, column) pairs with P(row = i) and
-    P(col = j) proportional to the power-law weights (the fast Chung-Lu
-    sampler); repeated pairs are dropped, which caps every row at n entries.
-    Node labels are shuffled so heavy rows/columns are not clustered."""
+    Edges are drawn as oversample * z independent (row, column) pairs with
+    P(row = i) and P(col = j) proportional to the power-law weights (the fast
+    Chung-Lu sampler); repeated pairs are dropped (about 16% of the draws at
+    these sizes, hence the oversampling), which also caps every row at n
+    entries.  Node labels are shuffled so heavy rows/columns are not clustered."""
     rng = np.random.default_rng(seed)
     wr = _power_law_weights(m, exponent, z)
     wc = _power_law_weights(n, exponent, z)
+    z = int(round(z * oversample))
     rperm = rng.permutation(m)
     cperm = rng.permutation(n)
     cr = np.cumsum(wr); cr /= cr[-1]

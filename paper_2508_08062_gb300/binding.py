@@ -30,7 +30,8 @@ PRECISIONS = {"fp64": FP64, "mixed": MIXED}
 EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_estimate_norm",
            "aapdhg_set_method", "aapdhg_set_start", "aapdhg_reset", "aapdhg_iterate",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
-           "aapdhg_get_trace", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
+           "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
+           "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
 
 
 class AAPDHGError(RuntimeError):
@@ -68,6 +69,8 @@ def load(path: str = LIB_PATH):
     L.aapdhg_get_counters.argtypes = [vp, vp, vp, vp, vp]
     L.aapdhg_set_trace.argtypes = [vp, i64]
     L.aapdhg_get_trace.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
+    L.aapdhg_profile_kernels.argtypes = [vp, i32]
+    L.aapdhg_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
     L.aapdhg_device_bytes.argtypes = [vp, C.POINTER(i64)]
     L.aapdhg_last_error.argtypes = [vp]
     L.aapdhg_last_error.restype = C.c_char_p
@@ -244,6 +247,26 @@ class Solver:
                                              _ptr(mk)))
         k = n.value
         return dict(branch=br[:k], gnorm=gn[:k], kkt=kk[:k], mk=mk[:k])
+
+    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix")
+
+    def profile_kernels(self, enable=True):
+        """CUDA-event timing of every kernel launched by iterate (resets totals)."""
+        self._check(self._L.aapdhg_profile_kernels(self._h, int(bool(enable))))
+
+    def kernel_profile(self):
+        out = {}
+        for k, name in enumerate(self.KERNEL_KINDS):
+            n, ms = C.c_int64(), C.c_double()
+            self._check(self._L.aapdhg_get_kernel_profile(self._h, k, C.byref(n), C.byref(ms)))
+            out[name] = dict(launches=n.value, total_ms=ms.value,
+                             avg_ms=(ms.value / n.value) if n.value else None)
+        return out
+
+    def launch_count(self):
+        n, ms = C.c_int64(), C.c_double()
+        self._check(self._L.aapdhg_get_kernel_profile(self._h, -1, C.byref(n), C.byref(ms)))
+        return n.value
 
     def device_bytes(self):
         b = C.c_int64()

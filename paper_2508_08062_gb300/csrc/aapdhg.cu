@@ -124,6 +124,13 @@ struct aapdhg_s {
     DevState *st_host = nullptr;           // pinned mirror
     // trace
     int64_t tr_cap = 0;
+    // kernel instrumentation (CUDA events on the handle's stream)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    double prof_ms[4] = {0, 0, 0, 0};
+    int64_t prof_n[4] = {0, 0, 0, 0};
+    int64_t launches = 0;
     // raw device pointers kept for re-initialisation
     void *d_UP = nullptr;
     void *d_lo = nullptr;
@@ -288,6 +295,39 @@ int grid_for(aapdhg_t h, int64_t blocks_needed, int occ) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, cap));
 }
 
+// Kernel kinds of the instrumentation.
+enum { KIND_XSTEP = 0, KIND_YSTEP = 1, KIND_MEMORY = 2, KIND_MIX = 3 };
+
+void mark_begin(aapdhg_t h, int kind) {
+    h->launches += 1;
+    if (!h->prof_on) return;
+    const size_t need = 2 * (h->ev_kind.size() + 1);
+    while (h->ev.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { h->prof_on = false; return; }
+        h->ev.push_back(e);
+    }
+    cudaEventRecord(h->ev[2 * h->ev_kind.size()], h->stream);
+    h->ev_kind.push_back(kind);
+}
+
+void mark_end(aapdhg_t h) {
+    if (!h->prof_on || h->ev_kind.empty()) return;
+    cudaEventRecord(h->ev[2 * h->ev_kind.size() - 1], h->stream);
+}
+
+// Fold the recorded event pairs into the totals (after a stream sync).
+void collect_marks(aapdhg_t h) {
+    for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+            h->prof_ms[h->ev_kind[i]] += ms;
+            h->prof_n[h->ev_kind[i]] += 1;
+        }
+    }
+    h->ev_kind.clear();
+}
+
 template <typename V>
 aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, const int8_t *sense,
                            const double *q, const double *c, const double *lb, const double *ub) {
@@ -439,19 +479,26 @@ template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode) {
     Prob<V> &P = prob<V>(h);
     const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
     const int g3 = M > 0 ? P.grid3 : 1;
+    mark_begin(h, KIND_MEMORY);
     k_memory<V, MC><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-    if (mode == MODE_ITER && M > 0) k_mix<V, MC><<<h->grid5, BLOCK, 0, h->stream>>>(P, h->mp);
+    mark_end(h);
+    if (mode == MODE_ITER && M > 0) {
+        mark_begin(h, KIND_MIX);
+        k_mix<V, MC><<<h->grid5, BLOCK, 0, h->stream>>>(P, h->mp);
+        mark_end(h);
+    }
 }
 
 template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
     Prob<V> &P = prob<V>(h);
-    if (kkt) {
-        k_xstep<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-        k_ystep<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-    } else {
-        k_xstep<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-        k_ystep<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-    }
+    mark_begin(h, KIND_XSTEP);
+    if (kkt) k_xstep<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else k_xstep<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    mark_end(h);
+    mark_begin(h, KIND_YSTEP);
+    if (kkt) k_ystep<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else k_ystep<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    mark_end(h);
 }
 
 template <typename V> void launch_memory_any(aapdhg_t h, int mode) {
@@ -467,9 +514,11 @@ template <typename V> void launch_iteration(aapdhg_t h, bool kkt, int mode) {
     if (mode != MODE_EVAL) launch_memory_any<V>(h, mode);
 }
 
-aapdhg_status read_state(aapdhg_t h) {
-    CK(h, cudaMemcpyAsync(h->st_host, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+aapdhg_status read_state(aapdhg_t h, bool full = true) {
+    const size_t bytes = full ? sizeof(DevState) : offsetof(DevState, list);
+    CK(h, cudaMemcpyAsync(h->st_host, h->st, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
+    collect_marks(h);
     return AAPDHG_OK;
 }
 
@@ -501,7 +550,7 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
         }
         CK(h, cudaGetLastError());
         launched += chunk;
-        if ((s = read_state(h)) != AAPDHG_OK) return s;
+        if ((s = read_state(h, false)) != AAPDHG_OK) return s;
         if (h->st_host->error) return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
         done = h->st_host->done != 0;
         hit = h->st_host->it;
@@ -855,6 +904,32 @@ aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double 
     return AAPDHG_OK;
 }
 
+aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    CK(h, cudaStreamSynchronize(h->stream));
+    collect_marks(h);
+    h->prof_on = enable != 0;
+    for (int k = 0; k < 4; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
+                                        double *total_ms) {
+    if (!h || kind < -1 || kind > 3) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    CK(h, cudaStreamSynchronize(h->stream));
+    collect_marks(h);
+    if (kind == -1) {
+        if (launches) *launches = h->launches;
+        if (total_ms) *total_ms = 0.0;
+    } else {
+        if (launches) *launches = h->prof_n[kind];
+        if (total_ms) *total_ms = h->prof_ms[kind];
+    }
+    return AAPDHG_OK;
+}
+
 aapdhg_status aapdhg_device_bytes(aapdhg_t h, int64_t *bytes) {
     if (!h || !bytes) return AAPDHG_ERR_INVALID;
     *bytes = h->bytes;
@@ -869,6 +944,7 @@ const char *aapdhg_last_error(aapdhg_t h) {
 void aapdhg_destroy(aapdhg_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
     dev_free_all(h);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

@@ -31,8 +31,6 @@ void *g_ctx = nullptr;
 thread_local std::string g_create_err;
 
 constexpr int CHUNK_ITERS = 64;   // iterations launched between two host polls
-constexpr int LPR_ITEMS = 4;      // target entries per lane when choosing lanes per row
-constexpr int LONG_ROW = 32 * 32; // rows longer than this are split into chunks
 
 struct HostCSR {
     int32_t rows = 0;
@@ -40,53 +38,54 @@ struct HostCSR {
     std::vector<double> val;
 };
 
-// Per-matrix device-side tables built on the host.
-struct SegHost {
-    SegTable t{};
+// Per-matrix device-side tables built on the host: chunk tables of the long
+// rows and the SELL-32 slices of the short rows (rows sorted longest first).
+struct LayoutHost {
+    int32_t n_long = 0, n_chunks = 0, n_slices = 0;
     std::vector<int32_t> chunk_row, row_chunk0;
+    std::vector<int32_t> slice_ptr, slice_w, sell_ci;
+    std::vector<double> sell_val;
 };
 
-SegHost build_segments(const HostCSR &A) {
-    SegHost S;
-    S.t.nseg = 0;
+LayoutHost build_layout(const HostCSR &A) {
+    LayoutHost L;
     const int32_t R = A.rows;
     auto len = [&](int32_t r) { return A.rp[r + 1] - A.rp[r]; };
-    // split rows: rows are sorted longest first, so they form a prefix
     int32_t nlong = 0;
-    while (nlong < R && len(nlong) > LONG_ROW) ++nlong;
-    S.row_chunk0.assign(nlong + 1, 0);
+    while (nlong < R && len(nlong) > SELL_MAX) ++nlong;
+    L.row_chunk0.assign(nlong + 1, 0);
     for (int32_t r = 0; r < nlong; ++r) {
         const int32_t nch = (len(r) + LONG_CHUNK - 1) / LONG_CHUNK;
-        S.row_chunk0[r + 1] = S.row_chunk0[r] + nch;
-        for (int32_t c = 0; c < nch; ++c) S.chunk_row.push_back(r);
+        L.row_chunk0[r + 1] = L.row_chunk0[r] + nch;
+        for (int32_t c = 0; c < nch; ++c) L.chunk_row.push_back(r);
     }
-    S.t.n_long = nlong;
-    S.t.n_chunks = S.row_chunk0[nlong];
-    int64_t tasks = 0;
-    int s = 0;
-    S.t.task0[0] = 0;
-    // segment 0: split rows (present even when empty so lpr 0 is always first)
-    S.t.lpr[s] = 0;
-    S.t.row0[s] = 0;
-    S.t.row1[s] = nlong;
-    tasks += S.t.n_chunks;
-    S.t.task0[++s] = tasks;
-    int32_t r = nlong;
-    for (int lpr = 32; lpr >= 1; lpr >>= 1) {
-        // rows whose length needs lpr lanes: len > (lpr/2) * LPR_ITEMS, or all rest for lpr = 1
-        const int32_t lo_len = (lpr == 1) ? -1 : (lpr / 2) * LPR_ITEMS;
-        const int32_t r0 = r;
-        while (r < R && len(r) > lo_len) ++r;
-        if (r == r0) continue;
-        S.t.lpr[s] = lpr;
-        S.t.row0[s] = r0;
-        S.t.row1[s] = r;
-        const int32_t rpw = 32 / lpr;
-        tasks += (int64_t)((r - r0) + rpw - 1) / rpw;
-        S.t.task0[++s] = tasks;
+    L.n_long = nlong;
+    L.n_chunks = L.row_chunk0[nlong];
+    const int32_t nshort = R - nlong;
+    L.n_slices = (nshort + 31) / 32;
+    L.slice_ptr.resize(L.n_slices + 1, 0);
+    L.slice_w.resize(L.n_slices, 0);
+    for (int32_t s = 0; s < L.n_slices; ++s) {
+        const int32_t r0 = nlong + 32 * s;
+        L.slice_w[s] = len(r0);                 // longest row of the slice comes first
+        L.slice_ptr[s + 1] = L.slice_ptr[s] + 32 * L.slice_w[s];
     }
-    S.t.nseg = s;
-    return S;
+    const int64_t total = L.slice_ptr[L.n_slices];
+    L.sell_ci.assign(total, 0);
+    L.sell_val.assign(total, 0.0);
+    for (int32_t s = 0; s < L.n_slices; ++s) {
+        for (int32_t lane = 0; lane < 32; ++lane) {
+            const int32_t r = nlong + 32 * s + lane;
+            if (r >= R) break;
+            const int32_t lr = len(r);
+            for (int32_t t = 0; t < lr; ++t) {
+                const int64_t q = (int64_t)L.slice_ptr[s] + (int64_t)t * 32 + lane;
+                L.sell_ci[q] = A.ci[A.rp[r] + t];
+                L.sell_val[q] = A.val[A.rp[r] + t];
+            }
+        }
+    }
+    return L;
 }
 
 }  // namespace
@@ -346,28 +345,38 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
         for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
         return o;
     };
-    auto mk_csr = [&](const HostCSR &A, CSRView<V> &view, SegHost &sh) {
-        sh = build_segments(A);
+    auto mk_csr = [&](const HostCSR &A, CSRView<V> &view) {
+        LayoutHost L = build_layout(A);
         view.rows = A.rows;
         view.rp = alloc_copy(h, A.rp.data(), A.rp.size(), &ok);
         view.ci = alloc_copy(h, A.ci.data(), std::max<size_t>(A.ci.size(), 1), &ok);
         std::vector<V> v = to_v(A.val);
         if (v.empty()) v.push_back(V(0));
         view.val = alloc_copy(h, v.data(), v.size(), &ok);
-        view.seg = sh.t;
-        std::vector<int32_t> cr = sh.chunk_row;
-        if (cr.empty()) cr.push_back(0);
-        view.seg.chunk_row = alloc_copy(h, cr.data(), cr.size(), &ok);
-        view.seg.row_chunk0 = alloc_copy(h, sh.row_chunk0.data(), sh.row_chunk0.size(), &ok);
-        view.chunk_part = (V *)dev_alloc(h, sizeof(V) * 2 * std::max(1, sh.t.n_chunks));
-        view.chunk_cnt = (uint32_t *)dev_alloc(h, sizeof(uint32_t) * std::max(1, sh.t.n_long));
+        view.n_long = L.n_long;
+        view.n_chunks = L.n_chunks;
+        view.n_slices = L.n_slices;
+        auto nonempty = [](std::vector<int32_t> x) { if (x.empty()) x.push_back(0); return x; };
+        std::vector<int32_t> cr = nonempty(L.chunk_row), sci = nonempty(L.sell_ci);
+        std::vector<int2> meta(std::max(1, L.n_slices));
+        for (int32_t q = 0; q < L.n_slices; ++q) meta[q] = make_int2(L.slice_ptr[q], L.slice_w[q]);
+        view.chunk_row = alloc_copy(h, cr.data(), cr.size(), &ok);
+        view.row_chunk0 = alloc_copy(h, L.row_chunk0.data(), L.row_chunk0.size(), &ok);
+        view.slice_meta = alloc_copy(h, meta.data(), meta.size(), &ok);
+        view.sell_ci = alloc_copy(h, sci.data(), sci.size(), &ok);
+        std::vector<V> sv = to_v(L.sell_val);
+        if (sv.empty()) sv.push_back(V(0));
+        view.sell_val = alloc_copy(h, sv.data(), sv.size(), &ok);
+        view.chunk_part = (V *)dev_alloc(h, sizeof(V) * 2 * std::max(1, L.n_chunks));
+        view.chunk_cnt = (uint32_t *)dev_alloc(h, sizeof(uint32_t) * std::max(1, L.n_long));
         if (!view.chunk_part || !view.chunk_cnt) ok = false;
-        else if (cudaMemsetAsync(view.chunk_cnt, 0, sizeof(uint32_t) * std::max(1, sh.t.n_long),
+        else if (cudaMemsetAsync(view.chunk_cnt, 0, sizeof(uint32_t) * std::max(1, L.n_long),
                                  h->stream) != cudaSuccess) ok = false;
+        // the host vectors above are pageable: make the copies complete before they go
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
     };
-    SegHost sT, sK;
-    mk_csr(KT, P.KT, sT);
-    mk_csr(K, P.K, sK);
+    mk_csr(KT, P.KT);
+    mk_csr(K, P.K);
     (void)Z;
 
     // vectors in internal order
@@ -398,15 +407,15 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     int occ1 = 0, occ2 = 0, occ3 = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep<V, true>, BLOCK, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep<V, true>, BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, MAXM>, BLOCK, 0);
-    const int64_t tasksT = P.KT.seg.task0[P.KT.seg.nseg], tasksK = P.K.seg.task0[P.K.seg.nseg];
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, 20>, BLOCK, 0);
+    const int64_t tasksT = P.KT.ntasks(), tasksK = P.K.ntasks();
     P.grid1 = grid_for(h, (tasksT + WARPS - 1) / WARPS, occ1);
     P.grid2 = grid_for(h, (tasksK + WARPS - 1) / WARPS, occ2);
     P.grid3 = grid_for(h, (N + BLOCK - 1) / BLOCK, std::max(occ3, 1));
     h->grid5 = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
     P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * P.grid1);
     P.part2 = (double *)dev_alloc(h, sizeof(double) * 3 * P.grid2);
-    P.part3 = (double *)dev_alloc(h, sizeof(double) * (MAXM + 3) * std::max(P.grid3, h->grid5));
+    P.part3 = (double *)dev_alloc(h, sizeof(double) * (MAXM + 3) * h->sm_count * 8);
     h->st = (DevState *)dev_alloc(h, sizeof(DevState));
     P.st = h->st;
     if (!P.part1 || !P.part2 || !P.part3 || !h->st) ok = false;
@@ -478,13 +487,24 @@ aapdhg_status reset_any(aapdhg_t h) {
 template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode) {
     Prob<V> &P = prob<V>(h);
     const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
-    const int g3 = M > 0 ? P.grid3 : 1;
+    // grid of the memory pass for this instance: all resident blocks (fixed per
+    // instance, so its block partials are summed in a fixed order)
+    static int occ_mem = 0, occ_mix = 0;
+    if (occ_mem == 0) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_mem, k_memory<V, MC>, BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_mix, k_mix<V, MC>, BLOCK, 0);
+        occ_mem = std::max(occ_mem, 1);
+        occ_mix = std::max(occ_mix, 1);
+    }
+    P.grid3 = M > 0 ? grid_for(h, (h->N + BLOCK * 4 - 1) / (BLOCK * 4), occ_mem) : 1;
+    const int g5 = grid_for(h, (h->N + BLOCK * 4 - 1) / (BLOCK * 4), occ_mix);
+    const int g3 = P.grid3;
     mark_begin(h, KIND_MEMORY);
     k_memory<V, MC><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode);
     mark_end(h);
     if (mode == MODE_ITER && M > 0) {
         mark_begin(h, KIND_MIX);
-        k_mix<V, MC><<<h->grid5, BLOCK, 0, h->stream>>>(P, h->mp);
+        k_mix<V, MC><<<g5, BLOCK, 0, h->stream>>>(P, h->mp);
         mark_end(h);
     }
 }
@@ -506,6 +526,7 @@ template <typename V> void launch_memory_any(aapdhg_t h, int mode) {
     if (M <= 4) launch_memory_mix<V, 4>(h, mode);
     else if (M <= 8) launch_memory_mix<V, 8>(h, mode);
     else if (M <= 16) launch_memory_mix<V, 16>(h, mode);
+    else if (M <= 20) launch_memory_mix<V, 20>(h, mode);
     else launch_memory_mix<V, 32>(h, mode);
 }
 

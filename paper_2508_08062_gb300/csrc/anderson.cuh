@@ -197,16 +197,71 @@ __device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, Sol
 }
 
 // ---------------------------------------------------------------------------
+// Per-element work of the memory pass on W consecutive elements at e0.  The
+// old columns are read in groups of 8 with all loads of a group issued before
+// their use; the ring is read with evict-first loads (once per iteration).
+// ---------------------------------------------------------------------------
+constexpr int COLGRP = 8;
+
+template <typename V, int MC, int W>
+__device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int cur, bool prev_acc,
+                                             V beta, V *DGn, V *Wn, const int64_t *off, int nold,
+                                             Acc<V> (&acc)[MC + 3]) {
+    const V *UPs = reinterpret_cast<const V *>(P.UP);
+    const Pack<V, W> pa = ld<V, W>(UPs + 2 * e0), pb = ld<V, W>(UPs + 2 * e0 + W);
+    const Pack<V, W> gp = ld<V, W>(P.g + e0);
+    const Pack<V, W> dh = ld<V, W>(P.dh + e0);
+    Pack<V, W> wn;
+    if (prev_acc) wn = ld_stream<V, W>(Wn + e0);
+    Pack<V, W> gk, dgk, wk;
+    V dg[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int i0 = 2 * i, i1 = 2 * i + 1;
+        const V c0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
+        const V c1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
+        const V u = cur ? c1 : c0, uh = cur ? c0 : c1;
+        const V g = uh - u;
+        dg[i] = g - gp.v[i];
+        const V du = prev_acc ? wn.v[i] : gp.v[i];     // u^k - u^{k-1}
+        gk.v[i] = g;
+        dgk.v[i] = dg[i];
+        wk.v[i] = du + beta * dh.v[i] * dg[i];
+        acc[MC].add_sq(dg[i]);
+        acc[MC + 1].add_prod(dg[i], g);
+        acc[MC + 2].add_sq(du);
+    }
+    st<V, W>(P.g + e0, gk);
+    st<V, W>(DGn + e0, dgk);
+    st<V, W>(Wn + e0, wk);
+#pragma unroll
+    for (int s0 = 0; s0 < MC; s0 += COLGRP) {
+        if (s0 >= nold) break;
+        Pack<V, W> col[COLGRP];
+#pragma unroll
+        for (int j = 0; j < COLGRP; ++j)
+            if (s0 + j < MC && s0 + j < nold) col[j] = ld_stream<V, W>(P.DG + off[s0 + j] + e0);
+#pragma unroll
+        for (int j = 0; j < COLGRP; ++j)
+            if (s0 + j < MC && s0 + j < nold)
+#pragma unroll
+                for (int i = 0; i < W; ++i) acc[s0 + j].add_prod(col[j].v[i], dg[i]);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_memory: the per-iteration memory pass.  MC >= m_A bounds the number of
 // old columns read (compile-time, so the partial sums stay in registers).
 // mode INIT: only g^0 = u^1 - u^0 is written.
 // ---------------------------------------------------------------------------
 template <typename V, int MC>
 __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, int mode) {
+    constexpr int W = 16 / sizeof(V);
     DevState *st = P.st;
     if (st->done | st->error) return;
     const int M = (mp.method == 0) ? 0 : mp.mem;
     __shared__ int s_old[NSLOT];
+    __shared__ int64_t s_off[NSLOT];
     __shared__ int s_nold, s_new, s_prev_acc;
     __shared__ double sh[WARPS * (MC + 3)];
     const int cur = (mode == MODE_INIT) ? 0 : (int)(st->it & 1) ^ 1;
@@ -242,6 +297,8 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
         s_prev_acc = st->accept;
     }
     __syncthreads();
+    if (threadIdx.x < NSLOT) s_off[threadIdx.x] = (int64_t)s_old[threadIdx.x < s_nold ? threadIdx.x : 0] * P.Npad;
+    __syncthreads();
     const int nold = s_nold, sn = s_new;
     const bool prev_acc = s_prev_acc != 0;
 
@@ -250,24 +307,12 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
         V *DGn = P.DG + (int64_t)sn * P.Npad;
         V *Wn = P.W + (int64_t)sn * P.Npad;
         const V beta = (V)mp.beta;
-        for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
-             e += (int64_t)gridDim.x * BLOCK) {
-            const typename Vec2<V>::T pr = P.UP[e];
-            const V u = comp<V>(pr, cur), uh = comp<V>(pr, 1 - cur);
-            const V g = uh - u;
-            const V gp = P.g[e];
-            const V dg = g - gp;
-            const V du = prev_acc ? Wn[e] : gp;     // u^k - u^{k-1}
-            P.g[e] = g;
-            DGn[e] = dg;
-            Wn[e] = du + beta * __ldg(P.dh + e) * dg;
-#pragma unroll
-            for (int s = 0; s < MC; ++s)
-                if (s < nold) acc[s].add_prod(__ldcs(P.DG + (int64_t)s_old[s] * P.Npad + e), dg);
-            acc[MC].add_sq(dg);
-            acc[MC + 1].add_prod(dg, g);
-            acc[MC + 2].add_sq(du);
-        }
+        const int64_t NV = P.N / W * W;
+        const int64_t stride = (int64_t)gridDim.x * BLOCK;
+        for (int64_t e0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) * W; e0 < NV; e0 += stride * W)
+            memory_elems<V, MC, W>(P, e0, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
+        for (int64_t e = NV + blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N; e += stride)
+            memory_elems<V, MC, 1>(P, e, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
         // block reduce -> partials
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -377,21 +422,66 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
 // over T(u^k), and du = u^{k+1} - u^k into the free slot (Alg. 2, the AA
 // branch; the projection P of Sec. 3 is a clamp to [lo, hi]).
 // ---------------------------------------------------------------------------
+template <typename V, int MC, int W>
+__device__ __forceinline__ void mix_elems(const Prob<V> &P, int64_t e0, int cur, V beta,
+                                          const V *gam, const int64_t *off, int k, V *Wf) {
+    V *UPs = reinterpret_cast<V *>(P.UP);
+    Pack<V, W> pa = ld<V, W>(UPs + 2 * e0), pb = ld<V, W>(UPs + 2 * e0 + W);
+    const Pack<V, W> dh = ld<V, W>(P.dh + e0);
+    const Pack<V, W> lo = ld<V, W>(P.lo + e0), hi = ld<V, W>(P.hi + e0);
+    V u[W], v[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int i0 = 2 * i, i1 = 2 * i + 1;
+        const V c0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
+        const V c1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
+        u[i] = cur ? c1 : c0;
+        const V uh = cur ? c0 : c1;
+        v[i] = u[i] + beta * dh.v[i] * (uh - u[i]);
+    }
+#pragma unroll
+    for (int t0 = 0; t0 < MC; t0 += COLGRP) {
+        if (t0 >= k) break;
+        Pack<V, W> col[COLGRP];
+#pragma unroll
+        for (int j = 0; j < COLGRP; ++j)
+            if (t0 + j < MC && t0 + j < k) col[j] = ld_stream<V, W>(P.W + off[t0 + j] + e0);
+#pragma unroll
+        for (int j = 0; j < COLGRP; ++j)
+            if (t0 + j < MC && t0 + j < k)
+#pragma unroll
+                for (int i = 0; i < W; ++i) v[i] = fma(-gam[t0 + j], col[j].v[i], v[i]);
+    }
+    Pack<V, W> du;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        V x = v[i] < lo.v[i] ? lo.v[i] : (v[i] > hi.v[i] ? hi.v[i] : v[i]);
+        du.v[i] = x - u[i];
+        const int slot = 2 * i + (1 - cur);             // overwrite T(u^k) with u^{k+1}
+        if (slot < W) pa.v[slot % W] = x; else pb.v[slot % W] = x;
+    }
+    st<V, W>(UPs + 2 * e0, pa);
+    st<V, W>(UPs + 2 * e0 + W, pb);
+    st<V, W>(Wf + e0, du);
+}
+
 template <typename V, int MC>
 __global__ void __launch_bounds__(BLOCK) k_mix(Prob<V> P, MethodParams mp) {
+    constexpr int W = 16 / sizeof(V);
     DevState *st = P.st;
     if (st->done | st->error) return;
     if (!st->accept) return;
     __shared__ V s_gam[MC];
-    __shared__ int s_use[MC];
+    __shared__ int64_t s_off[MC];
     __shared__ int s_k, s_free;
     if (threadIdx.x == 0) {
         s_k = st->use_count;
         s_free = st->free_slot;
     }
     if (threadIdx.x < MC) {
-        s_gam[threadIdx.x] = (threadIdx.x < st->use_count) ? (V)st->gamma[threadIdx.x] : V(0);
-        s_use[threadIdx.x] = (threadIdx.x < st->use_count) ? st->use[threadIdx.x] : 0;
+        const bool on = threadIdx.x < st->use_count;
+        s_gam[threadIdx.x] = on ? (V)st->gamma[threadIdx.x] : V(0);
+        s_off[threadIdx.x] = (int64_t)(on ? st->use[threadIdx.x] : 0) * P.Npad;
     }
     __syncthreads();
     const int k = s_k;
@@ -399,20 +489,12 @@ __global__ void __launch_bounds__(BLOCK) k_mix(Prob<V> P, MethodParams mp) {
     const int cur = (int)(st->it & 1);
     const V beta = (V)mp.beta;
     V *Wf = P.W + (int64_t)s_free * P.Npad;
-    for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
-         e += (int64_t)gridDim.x * BLOCK) {
-        typename Vec2<V>::T pr = P.UP[e];
-        const V u = comp<V>(pr, cur), uh = comp<V>(pr, 1 - cur);
-        V v = u + beta * __ldg(P.dh + e) * (uh - u);
-#pragma unroll
-        for (int t = 0; t < MC; ++t)
-            if (t < k) v = fma(-s_gam[t], __ldcs(P.W + (int64_t)s_use[t] * P.Npad + e), v);
-        const V l = __ldg(P.lo + e), h = __ldg(P.hi + e);
-        v = v < l ? l : (v > h ? h : v);
-        if (cur) pr.x = v; else pr.y = v;
-        P.UP[e] = pr;
-        Wf[e] = v - u;
-    }
+    const int64_t NV = P.N / W * W;
+    const int64_t stride = (int64_t)gridDim.x * BLOCK;
+    for (int64_t e0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) * W; e0 < NV; e0 += stride * W)
+        mix_elems<V, MC, W>(P, e0, cur, beta, s_gam, s_off, k, Wf);
+    for (int64_t e = NV + blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N; e += stride)
+        mix_elems<V, MC, 1>(P, e, cur, beta, s_gam, s_off, k, Wf);
 }
 
 }  // namespace aap

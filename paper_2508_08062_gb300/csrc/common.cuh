@@ -9,8 +9,10 @@ constexpr int MAXM = 32;            // largest Anderson memory m_A
 constexpr int NSLOT = MAXM + 1;     // ring slots: m_A columns + one slot for the next du
 constexpr int BLOCK = 256;          // threads per block of the streaming kernels
 constexpr int WARPS = BLOCK / 32;
-constexpr int LONG_CHUNK = 1024;    // nnz per warp task of a split (long) row
-constexpr int MAX_SEG = 8;          // long-row segment + lanes-per-row 32,16,8,4,2,1
+constexpr int LONG_CHUNK = 1024;    // entries per warp task of a long row
+constexpr int SELL_MAX = 32;        // rows up to this length go to SELL-32 slices
+constexpr int LOADS = 8;            // independent loads a lane keeps in flight
+constexpr int SLICES_PER_TASK = 2;  // SELL slices one warp reads in lockstep
 
 // ---------------------------------------------------------------------------
 // Accumulators.  FP64 mode: plain double.  Mixed mode: a float pair (hi, lo)
@@ -123,28 +125,31 @@ struct Trace {
     int32_t *mk;
 };
 
-// Lanes-per-row segments of one CSR matrix whose rows are sorted by length,
-// longest first.  Segment 0 holds the split rows (lpr == 0): each is cut
-// into LONG_CHUNK-sized chunks, one warp task per chunk.
-struct SegTable {
-    int32_t nseg;
-    int32_t lpr[MAX_SEG];
-    int32_t row0[MAX_SEG], row1[MAX_SEG];
-    int64_t task0[MAX_SEG + 1];   // prefix sums of warp tasks
-    int32_t n_long;               // split rows (rows [0, n_long))
-    int32_t n_chunks;
-    const int32_t *chunk_row;     // chunk -> row
-    const int32_t *row_chunk0;    // split row -> first chunk (n_long + 1 entries)
-};
-
+// One sparse matrix (K or K') with rows renumbered longest first, in two parts:
+//  - rows [0, n_long), longer than SELL_MAX entries: CSR, cut into chunks of
+//    at most LONG_CHUNK entries, one warp task per chunk (a row with several
+//    chunks is finished by the warp whose chunk arrives last);
+//  - rows [n_long, rows): SELL-32 slices of 32 consecutive rows stored column
+//    by column (entry t of the 32 rows contiguous), padded with zero entries
+//    (column 0, value 0) to the slice's longest row; one warp task per
+//    SLICES_PER_TASK consecutive slices, lane = row of each slice.
+// The full CSR (rp, ci, val) is kept for the set-up kernels.
 template <typename V> struct CSRView {
     int32_t rows;
     const int32_t *rp;
     const int32_t *ci;
     const V *val;
-    SegTable seg;
+    int32_t n_long, n_chunks, n_slices;
+    const int32_t *chunk_row;     // chunk -> row
+    const int32_t *row_chunk0;    // split row -> first chunk (n_long + 1 entries)
+    const int2 *slice_meta;       // slice -> (offset of its first entry in sell_*, width)
+    const int32_t *sell_ci;
+    const V *sell_val;
     V *chunk_part;                // n_chunks * 2 partial sums of split rows
     uint32_t *chunk_cnt;          // n_long arrival counters (self-resetting)
+    __host__ __device__ int64_t ntasks() const {
+        return (int64_t)n_chunks + (n_slices + SLICES_PER_TASK - 1) / SLICES_PER_TASK;
+    }
 };
 
 // Everything a kernel needs about the problem and the iterate buffers.
@@ -171,6 +176,34 @@ template <typename V> struct Prob {
 // receives T(u^k).  The roles swap every iteration, so a PDHG step never copies.
 template <typename V>
 __device__ __forceinline__ V comp(const typename Vec2<V>::T &p, int c) { return c ? p.y : p.x; }
+
+// W consecutive elements, loaded / stored as one 16-byte vector when W*sizeof(V) == 16.
+template <typename V, int W> struct alignas(sizeof(V) * W) Pack { V v[W]; };
+
+template <typename V, int W>
+__device__ __forceinline__ Pack<V, W> ld(const V *p) { return *reinterpret_cast<const Pack<V, W> *>(p); }
+
+// Streaming (evict-first) load: data read once per iteration.
+template <typename V, int W>
+__device__ __forceinline__ Pack<V, W> ld_stream(const V *p) {
+    Pack<V, W> r;
+    if constexpr (W * sizeof(V) == 16) {
+        if constexpr (sizeof(V) == 4) {
+            const float4 t = __ldcs(reinterpret_cast<const float4 *>(p));
+            r.v[0] = t.x; r.v[1] = t.y; r.v[2] = t.z; r.v[3] = t.w;
+        } else {
+            const double2 t = __ldcs(reinterpret_cast<const double2 *>(p));
+            r.v[0] = t.x; r.v[1] = t.y;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < W; ++i) r.v[i] = __ldcs(p + i);
+    }
+    return r;
+}
+
+template <typename V, int W>
+__device__ __forceinline__ void st(V *p, const Pack<V, W> &v) { *reinterpret_cast<Pack<V, W> *>(p) = v; }
 
 // Kernel modes: forming u^1 = T u^0 and g^0, a loop iteration, or a KKT
 // evaluation of the current iterate that changes no run state.
@@ -209,6 +242,35 @@ __device__ __forceinline__ bool last_block(uint32_t *cnt) {
     __syncthreads();
     if (is_last) __threadfence();
     return is_last;
+}
+
+// Fixed-order FP64 sums over `nb` blocks of columns [0, NC) of part[nb][stride]
+// in one pass (one load round, warp shuffles, one shared-memory stage), by one
+// block; out[k] valid in every thread on return.
+template <int NC>
+__device__ __forceinline__ void block_sum_columns(const double *part, int nb, int stride,
+                                                  double (&out)[NC], double *sh) {
+    double s[NC];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) s[k] = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int k = 0; k < NC; ++k) s[k] += __ldcg(part + (int64_t)b * stride + k);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+#pragma unroll
+        for (int o = 16; o; o >>= 1) s[k] += __shfl_xor_sync(0xffffffffu, s[k], o);
+        if (lane == 0) sh[warp * NC + k] = s[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NC; ++k) {
+        double t = 0.0;
+        for (int w = 0; w < nw; ++w) t += sh[w * NC + k];
+        out[k] = t;
+    }
+    __syncthreads();
 }
 
 // Fixed-order FP64 sum over `nb` blocks of column k of part[nb][stride], by

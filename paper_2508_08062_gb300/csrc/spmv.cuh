@@ -1,12 +1,13 @@
 // Fused PDHG half-steps (Sec. 3, eq. pdhg) on row-sliced CSR matrices.
 //
-// Both K and K' are stored as CSR with rows renumbered longest-first.  Rows are
-// grouped in segments of equal "lanes per row" (lpr = 32, 16, ..., 1): a warp
-// task covers 32 / lpr consecutive rows, each row read by lpr lanes with
-// coalesced loads of its values and indices.  Rows longer than 32 * 32
-// entries are split into LONG_CHUNK-entry chunks, one warp task each; the warp
-// that finishes the last chunk of a row sums the chunk partials in chunk order
-// (deterministic) and runs the row epilogue.
+// Both K and K' are stored with rows renumbered longest first.  Rows longer
+// than SELL_MAX entries are read as CSR in chunks of LONG_CHUNK entries, one
+// warp per chunk with coalesced loads; the warp that finishes the last chunk
+// of a row sums the chunk partials in chunk order (deterministic) and runs the
+// row epilogue.  Shorter rows are stored as SELL-32 slices (32 rows of
+// similar length, column by column): a warp reads one slice with fully
+// coalesced, mutually independent index/value loads and issues all gathers of
+// a step together, lane = row, so the epilogue is coalesced too.
 //
 // The x-step kernel computes, per variable j,
 //     s_j = (K'y)_j,  xh_j = P_X(x_j - tau (c_j - s_j))
@@ -25,34 +26,47 @@
 namespace aap {
 
 // Process warp task t of matrix A.  gather(col, val, acc) folds one entry
-// into the NACC per-lane partial sums; epi(row, acc) runs once per row on one
-// lane with the row's complete sums.
+// into the NACC per-lane partial sums.  The epilogue has two halves:
+// epi.pre(row) loads the row's own inputs (issued before the sum, since they
+// do not depend on it) and epi(row, pre, sums) finishes the row on one lane.
 template <typename V, int NACC, class Gather, class Epi>
 __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather &gather, Epi &epi) {
+    typedef typename Epi::Pre Pre;
     const int lane = threadIdx.x & 31;
-    const SegTable &S = A.seg;
-    int s = 0;
-#pragma unroll 1
-    while (s + 1 < S.nseg && t >= S.task0[s + 1]) ++s;
-    const int64_t lt = t - S.task0[s];
-    const int lpr = S.lpr[s];
-    V acc[NACC];
-#pragma unroll
-    for (int a = 0; a < NACC; ++a) acc[a] = V(0);
 
-    if (lpr == 0) {                                   // chunk of a split row
-        const int chunk = (int)lt;
-        const int r = __ldg(S.chunk_row + chunk);
-        const int c0 = __ldg(S.row_chunk0 + r);
-        const int nch = __ldg(S.row_chunk0 + r + 1) - c0;
+    if (t < A.n_chunks) {                               // chunk of a long row
+        V acc[NACC];
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a] = V(0);
+        const int chunk = (int)t;
+        const int r = __ldg(A.chunk_row + chunk);
+        const int c0 = __ldg(A.row_chunk0 + r);
+        const int nch = __ldg(A.row_chunk0 + r + 1) - c0;
         const int k0 = __ldg(A.rp + r) + (chunk - c0) * LONG_CHUNK;
         const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
-#pragma unroll 4
-        for (int k = k0 + lane; k < k1; k += 32) gather(__ldg(A.ci + k), __ldg(A.val + k), acc);
+        Pre pre;
+        if (nch == 1 && lane == 0) pre = epi.pre(r);
+        for (int kb = k0 + lane; kb < k1; kb += 32 * LOADS) {
+            int ci[LOADS];
+            V va[LOADS];
+#pragma unroll
+            for (int j = 0; j < LOADS; ++j) {
+                const int k = kb + 32 * j;
+                ci[j] = k < k1 ? __ldcs(A.ci + k) : 0;
+                va[j] = k < k1 ? __ldcs(A.val + k) : V(0);
+            }
+#pragma unroll
+            for (int j = 0; j < LOADS; ++j)
+                if (kb + 32 * j < k1) gather(ci[j], va[j], acc);
+        }
 #pragma unroll
         for (int a = 0; a < NACC; ++a)
 #pragma unroll
             for (int o = 16; o; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+        if (nch == 1) {
+            if (lane == 0) epi(r, pre, acc);
+            return;
+        }
         int last = 0;
         if (lane == 0) {
 #pragma unroll
@@ -63,6 +77,7 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last && lane == 0) {
             __threadfence();
+            pre = epi.pre(r);
             V tot[NACC];
 #pragma unroll
             for (int a = 0; a < NACC; ++a) tot[a] = V(0);
@@ -70,24 +85,56 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
 #pragma unroll
                 for (int a = 0; a < NACC; ++a) tot[a] += __ldcg(A.chunk_part + (int64_t)c * 2 + a);
             A.chunk_cnt[r] = 0u;
-            epi(r, tot);
+            epi(r, pre, tot);
         }
         return;
     }
 
-    const int rpw = 32 / lpr;
-    const int r = S.row0[s] + (int)(lt * rpw) + lane / lpr;
-    const int sub = lane & (lpr - 1);
-    const bool valid = r < S.row1[s];
-    if (valid) {
-        const int k0 = __ldg(A.rp + r), k1 = __ldg(A.rp + r + 1);
-#pragma unroll 4
-        for (int k = k0 + sub; k < k1; k += lpr) gather(__ldg(A.ci + k), __ldg(A.val + k), acc);
-    }
-    for (int o = lpr >> 1; o; o >>= 1)
+    // SLICES_PER_TASK SELL-32 slices in lockstep: lane = row of each slice,
+    // entry tt of a slice's 32 rows contiguous; padding entries are zeros.
+    constexpr int G = SLICES_PER_TASK;
+    constexpr int B = LOADS / G;
+    const int sl0 = (int)(t - A.n_chunks) * G;
+    int2 meta[G];
+    int r[G];
+    Pre pre[G];
+    V acc[G][NACC];
+    int wmax = 0;
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
-    if (valid && sub == 0) epi(r, acc);
+    for (int g = 0; g < G; ++g) {
+        const bool on = sl0 + g < A.n_slices;
+        meta[g] = on ? __ldg(A.slice_meta + sl0 + g) : make_int2(0, 0);
+        r[g] = A.n_long + (sl0 + g) * 32 + lane;
+        if (r[g] < A.rows) pre[g] = epi.pre(r[g]);
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[g][a] = V(0);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        meta[g].x += lane;
+        wmax = max(wmax, meta[g].y);
+    }
+    for (int t0 = 0; t0 < wmax; t0 += B) {
+        int ci[G][B];
+        V va[G][B];
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const bool on = t0 + j < meta[g].y;
+                const int q = meta[g].x + (t0 + j) * 32;
+                ci[g][j] = on ? __ldcs(A.sell_ci + q) : 0;
+                va[g][j] = on ? __ldcs(A.sell_val + q) : V(0);
+            }
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+            for (int j = 0; j < B; ++j)
+                if (t0 + j < meta[g].y) gather(ci[g][j], va[g][j], acc[g]);
+    }
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+        if (r[g] < A.rows) epi(r[g], pre[g], acc[g]);
 }
 
 // --------------------------------------------------------------------------
@@ -101,15 +148,19 @@ template <typename V> struct GatherY {
 };
 
 template <typename V, bool KKT> struct EpiX {
+    typedef typename Vec2<V>::T V2;
+    struct Pre { V2 pr; V c, l, u; };
     const Prob<V> &P;
     V tau;
     int cur;
     Acc<V> &g2, &dres2, &lam, &cx;
-    __device__ __forceinline__ void operator()(int j, const V (&s)[1]) {
-        typedef typename Vec2<V>::T V2;
-        V2 pr = P.UP[j];
+    __device__ __forceinline__ Pre pre(int j) const {
+        return Pre{P.UP[j], __ldg(P.c + j), __ldg(P.lo + j), __ldg(P.hi + j)};
+    }
+    __device__ __forceinline__ void operator()(int j, const Pre &in, const V (&s)[1]) {
+        V2 pr = in.pr;
         const V x = comp<V>(pr, cur);
-        const V cj = __ldg(P.c + j), l = __ldg(P.lo + j), u = __ldg(P.hi + j);
+        const V cj = in.c, l = in.l, u = in.u;
         const V r = cj - s[0];
         V xh = x - tau * r;
         xh = xh < l ? l : (xh > u ? u : xh);
@@ -142,7 +193,7 @@ __global__ void __launch_bounds__(BLOCK) k_xstep(Prob<V> P, MethodParams mp, int
     GatherY<V> gat{reinterpret_cast<const V *>(P.UP + P.n) + cur};
     EpiX<V, KKT> epi{P, (V)mp.tau, cur, g2, dres2, lam, cx};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.KT.seg.task0[P.KT.seg.nseg];
+    const int64_t ntask = P.KT.ntasks();
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
         if (t < ntask) run_task<V, 1>(P.KT, t, gat, epi);
@@ -167,15 +218,19 @@ template <typename V, bool KKT> struct GatherXZ {
 };
 
 template <typename V, bool KKT> struct EpiY {
+    typedef typename Vec2<V>::T V2;
+    struct Pre { V2 pr; V q, l; };
     const Prob<V> &P;
     V sigma;
     int cur;
     Acc<V> &g2, &pres2, &qy;
-    __device__ __forceinline__ void operator()(int i, const V (&t)[KKT ? 2 : 1]) {
-        typedef typename Vec2<V>::T V2;
-        V2 pr = P.UP[P.n + i];
+    __device__ __forceinline__ Pre pre(int i) const {
+        return Pre{P.UP[P.n + i], __ldg(P.q + i), __ldg(P.lo + P.n + i)};
+    }
+    __device__ __forceinline__ void operator()(int i, const Pre &in, const V (&t)[KKT ? 2 : 1]) {
+        V2 pr = in.pr;
         const V y = comp<V>(pr, cur);
-        const V qi = __ldg(P.q + i), l = __ldg(P.lo + P.n + i);
+        const V qi = in.q, l = in.l;
         V yh = y + sigma * (qi - t[0]);
         yh = yh < l ? l : yh;                       // P_Y: y_i >= 0 on '>=' rows
         if (cur) pr.x = yh; else pr.y = yh;
@@ -194,17 +249,12 @@ template <typename V, bool KKT> struct EpiY {
 // termination flag, safeguard decision of Alg. 2 / Alg. 3.
 template <typename V>
 __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, bool kkt) {
-    __shared__ double sh[BLOCK];
-    const double g2 = block_sum_partials(P.part1, P.grid1, 4, 0, sh) +
-                      block_sum_partials(P.part2, P.grid2, 3, 0, sh);
-    double dres2 = 0, lam = 0, cx = 0, pres2 = 0, qy = 0;
-    if (kkt) {
-        dres2 = block_sum_partials(P.part1, P.grid1, 4, 1, sh);
-        lam = block_sum_partials(P.part1, P.grid1, 4, 2, sh);
-        cx = block_sum_partials(P.part1, P.grid1, 4, 3, sh);
-        pres2 = block_sum_partials(P.part2, P.grid2, 3, 1, sh);
-        qy = block_sum_partials(P.part2, P.grid2, 3, 2, sh);
-    }
+    __shared__ double sh[WARPS * 4];
+    double a1[4], a2[3];
+    block_sum_columns<4>(P.part1, P.grid1, 4, a1, sh);
+    block_sum_columns<3>(P.part2, P.grid2, 3, a2, sh);
+    const double g2 = a1[0] + a2[0];
+    const double dres2 = a1[1], lam = a1[2], cx = a1[3], pres2 = a2[1], qy = a2[2];
     if (threadIdx.x != 0) return;
     DevState *st = P.st;
     const double gn = sqrt(g2);
@@ -251,7 +301,7 @@ __global__ void __launch_bounds__(BLOCK) k_ystep(Prob<V> P, MethodParams mp, int
     GatherXZ<V, KKT> gat{P.UP, cur};
     EpiY<V, KKT> epi{P, (V)mp.sigma, cur, g2, pres2, qy};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.K.seg.task0[P.K.seg.nseg];
+    const int64_t ntask = P.K.ntasks();
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
         if (t < ntask) run_task<V, KKT ? 2 : 1>(P.K, t, gat, epi);
@@ -271,9 +321,11 @@ template <typename V> struct GatherPlain {
     }
 };
 template <typename V> struct EpiStore {
+    struct Pre {};
     V *y;
     Acc<V> &n2;
-    __device__ __forceinline__ void operator()(int r, const V (&s)[1]) {
+    __device__ __forceinline__ Pre pre(int) const { return Pre{}; }
+    __device__ __forceinline__ void operator()(int r, const Pre &, const V (&s)[1]) {
         y[r] = s[0];
         n2.add_sq(s[0]);
     }
@@ -286,7 +338,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv_plain(CSRView<V> A, const V *x, 
     GatherPlain<V> gat{x};
     EpiStore<V> epi{y, n2};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = A.seg.task0[A.seg.nseg];
+    const int64_t ntask = A.ntasks();
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
         if (t < ntask) run_task<V, 1>(A, t, gat, epi);

@@ -142,14 +142,14 @@ class ClockSampler:
 
 def kernel_bytes(P, s_v, kind, M, iters, accepted, use_sum, prev_acc):
     """Algorithmic HBM bytes of `iters` launches of a kernel kind (see the design
-    notes for the per-unit figures): CSR values + int32 indices + row pointers,
-    compulsory gathers once, every vector read or written once."""
+    notes for the per-unit figures): matrix values + int32 indices, compulsory
+    gathers once, every vector read or written once (row metadata not counted)."""
     n, m, Z = P.n, P.m, P.nnz
     N = n + m
     if kind == "xstep":
-        return iters * (Z * (s_v + 4) + 4 * (n + 1) + s_v * m + 7 * s_v * n)
+        return iters * (Z * (s_v + 4) + s_v * m + 7 * s_v * n)
     if kind == "ystep":
-        return iters * (Z * (s_v + 4) + 4 * (m + 1) + 2 * s_v * n + 6 * s_v * m)
+        return iters * (Z * (s_v + 4) + 2 * s_v * n + 6 * s_v * m)
     if kind == "memory":
         nold = max(M - 1, 0)
         return (iters * N * s_v * (7 + nold) + prev_acc * N * s_v) if M > 0 else 0
@@ -187,16 +187,18 @@ def run_ours(args):
     s.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
     kkt_every = 64
 
-    # warm-up
-    s.iterate(args.warmup, tol=0.0, kkt_every=kkt_every)
-    c0 = s.counters()
-    l0 = s.launch_count()
-    barrier()
     dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     with ClockSampler(dev_id) as clk:
+        # warm-up (the sampler starts here so that it is running when timing starts)
+        s.iterate(args.warmup, tol=0.0, kkt_every=kkt_every)
+        time.sleep(0.5)
+        s.iterate(args.warmup, tol=0.0, kkt_every=kkt_every)
+        c0 = s.counters()
+        l0 = s.launch_count()
+        barrier()
         ev0.record(stream)
         s.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
         ev1.record(stream)
@@ -379,8 +381,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
-    ap.add_argument("--warmup", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -130,6 +130,18 @@ struct aapdhg_s {
     double prof_ms[4] = {0, 0, 0, 0};
     int64_t prof_n[4] = {0, 0, 0, 0};
     int64_t launches = 0;
+    // CUDA graphs of full chunks, keyed by the KKT phase of the chunk's first
+    // iteration; invalidated whenever kernel parameters change
+    cudaStream_t cap_stream = nullptr;
+    struct GraphEntry {
+        cudaGraphExec_t exec;
+        int64_t phase;
+        int32_t kkt_every;
+        double tol;
+    };
+    std::vector<GraphEntry> graphs;
+    bool use_graphs = true;
+    int32_t dhat_mode = -1;                // mode D-hat was last formed with
     // raw device pointers kept for re-initialisation
     void *d_UP = nullptr;
     void *d_lo = nullptr;
@@ -253,18 +265,21 @@ void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, 
 
 // D-hat of the Remark on its construction (mode 1) or the identity (mode 0):
 // per row of K' (a variable) and per row of K (a constraint),
-// sqrt(max(max |entry|, 1e-10)).
+// sqrt(max(max |entry|, 1e-10)).  One warp per row, lanes striding its entries.
 template <typename V>
 __global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mode, V *dh) {
     const int64_t N = (int64_t)n + m;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        if (mode == 0) { dh[e] = V(1); continue; }
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < N; e += warps) {
+        if (mode == 0) { if (lane == 0) dh[e] = V(1); continue; }
         const CSRView<V> &A = e < n ? KT : K;
         const int32_t r = (int32_t)(e < n ? e : e - n);
         double mx = 0.0;
-        for (int32_t k = A.rp[r]; k < A.rp[r + 1]; ++k) mx = fmax(mx, fabs((double)A.val[k]));
-        dh[e] = (V)sqrt(fmax(mx, 1e-10));
+        for (int32_t k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) mx = fmax(mx, fabs((double)A.val[k]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) dh[e] = (V)sqrt(fmax(mx, 1e-10));
     }
 }
 
@@ -411,6 +426,7 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     const int64_t tasksT = P.KT.ntasks(), tasksK = P.K.ntasks();
     P.grid1 = grid_for(h, (tasksT + WARPS - 1) / WARPS, occ1);
     P.grid2 = grid_for(h, (tasksK + WARPS - 1) / WARPS, occ2);
+
     P.grid3 = grid_for(h, (N + BLOCK - 1) / BLOCK, std::max(occ3, 1));
     h->grid5 = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
     P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * P.grid1);
@@ -426,7 +442,9 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
 
     // D-hat and the norms ||q||, ||c|| on the device
     const int gE = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
-    k_dhat<V><<<gE, BLOCK, 0, h->stream>>>(P.KT, P.K, n, m, 1, const_cast<V *>(P.dh));
+    k_dhat<V><<<grid_for(h, (N + WARPS - 1) / WARPS, 8), BLOCK, 0, h->stream>>>(P.KT, P.K, n, m, 1,
+                                                                             const_cast<V *>(P.dh));
+    h->dhat_mode = 1;
     k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.q, m, P.part3, h->st, 0);
     k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.c, n, P.part3, h->st, 1);
     CK(h, cudaGetLastError());
@@ -543,6 +561,58 @@ aapdhg_status read_state(aapdhg_t h, bool full = true) {
     return AAPDHG_OK;
 }
 
+void drop_graphs(aapdhg_t h) {
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+// Launch one full chunk of CHUNK_ITERS iterations starting at iteration `hit`
+// as a CUDA graph (captured once per KKT phase on a private stream, replayed
+// on the handle's stream).  Returns false when graphs are not usable.
+template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t kkt_every) {
+    if (!h->use_graphs || h->prof_on) return false;
+    const int64_t phase = kkt_every > 0 ? hit % kkt_every : 0;
+    const double tol = h->mp.tol;
+    for (auto &g : h->graphs)
+        if (g.phase == phase && g.kkt_every == kkt_every && g.tol == tol) {
+            if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+            h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 4 : 3);
+            return true;
+        }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->use_graphs = false;
+        return false;
+    }
+    if (h->graphs.size() >= 8) drop_graphs(h);
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const int64_t saved = h->launches;
+    if (ok) {
+        for (int64_t c = 0; c < CHUNK_ITERS; ++c) {
+            const bool kkt = kkt_every > 0 && ((hit + c) % kkt_every) == 0;
+            launch_iteration<V>(h, kkt, MODE_ITER);
+        }
+        ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess;
+    }
+    h->stream = user;
+    h->launches = saved;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        h->use_graphs = false;
+        return false;
+    }
+    h->graphs.push_back({exec, phase, kkt_every, tol});
+    if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+    h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 4 : 3);
+    return true;
+}
+
 template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, double tol,
                                               int32_t kkt_every, int64_t *done_iters) {
     Prob<V> &P = prob<V>(h);
@@ -564,10 +634,12 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
     bool done = false;
     while (launched < max_iters && !done) {
         const int64_t chunk = std::min<int64_t>(CHUNK_ITERS, max_iters - launched);
-        for (int64_t c = 0; c < chunk; ++c) {
-            const int64_t itc = hit + c;
-            const bool kkt = kkt_every > 0 && (itc % kkt_every) == 0;
-            launch_iteration<V>(h, kkt, MODE_ITER);
+        if (!(chunk == CHUNK_ITERS && launch_chunk_graph<V>(h, hit, kkt_every))) {
+            for (int64_t c = 0; c < chunk; ++c) {
+                const int64_t itc = hit + c;
+                const bool kkt = kkt_every > 0 && (itc % kkt_every) == 0;
+                launch_iteration<V>(h, kkt, MODE_ITER);
+            }
         }
         CK(h, cudaGetLastError());
         launched += chunk;
@@ -792,6 +864,7 @@ aapdhg_status aapdhg_set_steps(aapdhg_t h, double tau, double sigma) {
     h->mp.tau = tau;
     h->mp.sigma = sigma;
     h->have_steps = true;
+    drop_graphs(h);
     return reset_any(h);
 }
 
@@ -814,15 +887,19 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
     h->mp.method = method; h->mp.mem = m_A; h->mp.D = D; h->mp.eps = eps; h->mp.eta = eta;
     h->mp.beta = beta; h->mp.c_s = c_s; h->mp.kappa = kappa; h->mp.c_div = c_div;
     h->mp.faa_adaptive = faa_adaptive ? 1 : 0;
-    // D-hat recomputed on the device for the requested mode
-    const int gE = grid_for(h, (h->N + BLOCK - 1) / BLOCK, 4);
-    if (h->prec == AAPDHG_FP64)
-        k_dhat<double><<<gE, BLOCK, 0, h->stream>>>(h->pd.KT, h->pd.K, h->n, h->m, dhat_mode,
-                                                    const_cast<double *>(h->pd.dh));
-    else
-        k_dhat<float><<<gE, BLOCK, 0, h->stream>>>(h->pf.KT, h->pf.K, h->n, h->m, dhat_mode,
-                                                   const_cast<float *>(h->pf.dh));
-    CK(h, cudaGetLastError());
+    drop_graphs(h);
+    // D-hat recomputed on the device when the requested mode differs
+    if (dhat_mode != h->dhat_mode) {
+        const int gD = grid_for(h, (h->N + WARPS - 1) / WARPS, 8);
+        if (h->prec == AAPDHG_FP64)
+            k_dhat<double><<<gD, BLOCK, 0, h->stream>>>(h->pd.KT, h->pd.K, h->n, h->m, dhat_mode,
+                                                        const_cast<double *>(h->pd.dh));
+        else
+            k_dhat<float><<<gD, BLOCK, 0, h->stream>>>(h->pf.KT, h->pf.K, h->n, h->m, dhat_mode,
+                                                       const_cast<float *>(h->pf.dh));
+        CK(h, cudaGetLastError());
+        h->dhat_mode = dhat_mode;
+    }
     return reset_any(h);
 }
 
@@ -901,6 +978,7 @@ aapdhg_status aapdhg_set_trace(aapdhg_t h, int64_t capacity) {
     }
     h->pf.tr = tr;
     h->pd.tr = tr;
+    drop_graphs(h);
     h->tr_cap = capacity;
     return reset_any(h);
 }
@@ -966,6 +1044,8 @@ void aapdhg_destroy(aapdhg_t h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+    drop_graphs(h);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     dev_free_all(h);
     if (h->st_host) cudaFreeHost(h->st_host);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);

@@ -181,6 +181,48 @@ aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable);
 aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
                                         double *total_ms);
 
+/* KKT residuals of a given point without any device allocation.  The paper
+ * has no counterpart to this entry point; it exists for callers that cannot
+ * allocate device memory when they need the residuals: code running during
+ * CUDA stream capture (cudaMalloc is not capturable, cudaFree synchronises the
+ * device), latency-critical loops that must avoid the implicit device
+ * synchronisation of cudaMalloc / cudaFree, and programs whose device memory
+ * is owned by another framework's pool.  Its scratch (block partial sums and
+ * an arrival counter) is a fixed file-scope device array of
+ * AAPDHG_NOALLOC_MAX_BLOCKS * 8 doubles (1 MiB), held by every GPU that loads
+ * the library until the process exits.
+ *
+ * Inputs, all device memory of the current device, caller-owned, FP64 where
+ * real-valued, in the caller's row and column order:
+ *   m, n                      rows of K and variables (n >= 1)
+ *   row_ptr/col_idx/val       K = [G; A] as CSR (int64 row pointers, int32 columns)
+ *   t_row_ptr/t_col_idx/t_val K' as CSR (n rows)
+ *   row_sense, q, c, lb, ub   as in aapdhg_create
+ *   x (n), y (m)              the point
+ * Output: out6 (device, 6 doubles) = {r_p, r_d, r_g, KKT, c'x, dual objective},
+ * the quantities of aapdhg_get_kkt, written on cuda_stream (NULL = legacy
+ * default stream).  The call is asynchronous; it only checks arguments and
+ * enqueues work.
+ * Limits and errors: returns AAPDHG_ERR_INVALID without touching the device
+ * when ceil(n / 512) + ceil(m / 512) > AAPDHG_NOALLOC_MAX_BLOCKS (about 8.4M
+ * rows in total), when m < 0 or n < 1, or when a required pointer is NULL;
+ * AAPDHG_ERR_CUDA when the scratch address cannot be resolved or the launch
+ * fails.  aapdhg_last_error does not report this entry point.
+ * Set-up: the first call on each device resolves the scratch array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Calls share the one scratch array: two
+ * calls whose work overlaps on the same GPU (different streams, or graphs
+ * launched concurrently) race and give wrong results; each call clears the
+ * counter it needs before its kernel starts.                                  */
+enum { AAPDHG_NOALLOC_MAX_BLOCKS = 16384 };
+aapdhg_status aapdhg_kkt_noalloc(int32_t m, int32_t n, const int64_t *row_ptr,
+                                 const int32_t *col_idx, const double *val,
+                                 const int64_t *t_row_ptr, const int32_t *t_col_idx,
+                                 const double *t_val, const int8_t *row_sense, const double *q,
+                                 const double *c, const double *lb, const double *ub,
+                                 const double *x, const double *y, double *out6,
+                                 void *cuda_stream);
+
 /* Bytes of device memory held by the handle.                                 */
 aapdhg_status aapdhg_device_bytes(aapdhg_t h, int64_t *bytes);
 

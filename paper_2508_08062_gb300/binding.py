@@ -31,7 +31,7 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_set_method", "aapdhg_set_start", "aapdhg_reset", "aapdhg_iterate",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
            "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
-           "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
+           "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
 
 
 class AAPDHGError(RuntimeError):
@@ -71,6 +71,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_get_trace.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
     L.aapdhg_profile_kernels.argtypes = [vp, i32]
     L.aapdhg_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
+    L.aapdhg_kkt_noalloc.argtypes = [i32, i32] + [vp] * 15
     L.aapdhg_device_bytes.argtypes = [vp, C.POINTER(i64)]
     L.aapdhg_last_error.argtypes = [vp]
     L.aapdhg_last_error.restype = C.c_char_p

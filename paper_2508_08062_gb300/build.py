@@ -33,7 +33,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, os.path.join(SRC_DIR, "aapdhg.cu")]
+           "-o", tmp, os.path.join(SRC_DIR, "aapdhg.cu"), os.path.join(SRC_DIR, "kkt_noalloc.cu")]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     subprocess.check_call(cmd)

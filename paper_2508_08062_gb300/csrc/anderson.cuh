@@ -335,13 +335,18 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
 
     // ---- final reduction and the m x m work (one block) -------------------
     __shared__ double red[MC + 3];
-    __shared__ double shs[BLOCK];
     __shared__ SolveSmem sm;
     if (M > 0) {
-        for (int s = 0; s < MC + 3; ++s) {
+        // one warp per partial column, lanes striding the blocks, shuffle tree:
+        // a fixed summation order without block-wide barriers
+        const int wl = threadIdx.x & 31, ww = threadIdx.x >> 5;
+        for (int s = ww; s < MC + 3; s += WARPS) {
             if (s < nold || s >= MC) {
-                const double v = block_sum_partials(P.part3, P.grid3, MC + 3, s, shs);
-                if (threadIdx.x == 0) red[s] = v;
+                double v = 0.0;
+                for (int b = wl; b < P.grid3; b += 32) v += __ldcg(P.part3 + (int64_t)b * (MC + 3) + s);
+#pragma unroll
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (wl == 0) red[s] = v;
             }
         }
     }

@@ -239,8 +239,8 @@ def run_ours(args):
     traffic = None
     try:
         tf = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tf.get(args.workload, {}).get(dom)
-        if ent and ent.get("kernel_sources") == kernel_source_hash():
+        ent = tf.get(args.workload, {}).get(dom) if args.scale == 1.0 else None
+        if ent and ent.get("kernel_sources") == kernel_source_hash(dom):
             traffic = ent["dram_bytes_per_launch"]
     except Exception:
         pass
@@ -322,13 +322,18 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def kernel_source_hash():
+KERNEL_FILES = {"xstep": ("common.cuh", "spmv.cuh"), "ystep": ("common.cuh", "spmv.cuh"),
+                "memory": ("common.cuh", "anderson.cuh"), "mix": ("common.cuh", "anderson.cuh")}
+
+
+def kernel_source_hash(kind):
+    """Hash of the source files a kernel kind is built from (staleness check of
+    the committed ncu traffic figures)."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_2508_08062_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_FILES[kind]:
+        h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:12]
 
 

@@ -355,19 +355,19 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     const int lane = threadIdx.x;
     int accept = 0, lsfail = 0;
     if (M > 0) {
+        // Gram row / column of the new slot; incremental right-hand side
+        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
+        for (int t = lane; t < nold; t += 32) {
+            const int s = s_old[t];
+            st->G[s * NSLOT + sn] = red[t];
+            st->G[sn * NSLOT + s] = red[t];
+            st->rhs[s] += red[t];
+            st->list[t] = s;
+        }
         if (lane == 0) {
-            // Gram row / column of the new slot; incremental right-hand side
-            for (int t = 0; t < nold; ++t) {
-                const int s = s_old[t];
-                st->G[s * NSLOT + sn] = red[t];
-                st->G[sn * NSLOT + s] = red[t];
-                st->rhs[s] += red[t];
-            }
             st->G[sn * NSLOT + sn] = red[MC];
             st->rhs[sn] = red[MC + 1];
             st->en2[sn] = red[MC + 2];
-            // list: keep the nold survivors, append the new column
-            for (int t = 0; t < nold; ++t) st->list[t] = s_old[t];
             st->list[nold] = sn;
             st->count = nold + 1;
             st->new_slot = sn;
@@ -391,23 +391,20 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
                 __syncwarp();
                 accept = ok ? 1 : 0;
                 lsfail = ok ? 0 : 1;
-                if (ok && mp.faa_adaptive && lane == 0) {
-                    for (int t = 0; t < nk; ++t) st->list[t] = sm.kept[t];
-                    st->count = nk;
+                if (ok && mp.faa_adaptive) {
+                    for (int t = lane; t < nk; t += 32) st->list[t] = sm.kept[t];
+                    if (lane == 0) st->count = nk;
                 }
             }
         }
         __syncwarp();
-        if (lane == 0) {
-            // slot for the next column's du: any slot not in the list
-            int fs = 0;
-            for (int cand = 0; cand < NSLOT; ++cand) {
-                bool used = false;
-                for (int t = 0; t < st->count; ++t) used = used || (st->list[t] == cand);
-                if (!used) { fs = cand; break; }
-            }
-            st->free_slot = fs;
-        }
+        // slot for the next column's du: the lowest slot not in the list
+        const int cnt = st->count;
+        unsigned long long used = 0ull;
+        for (int t = lane; t < cnt; t += 32) used |= 1ull << st->list[t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) used |= __shfl_xor_sync(0xffffffffu, used, o);
+        if (lane == 0) st->free_slot = __ffsll((long long)~used) - 1;
     }
     if (lane == 0) {
         const int64_t it = st->it;

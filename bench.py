@@ -181,6 +181,8 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     s = Solver(P, precision=wl["precision"], stream=stream)
+    if args.precondition:
+        s.set_scaling(10, True)
     nrm = s.estimate_norm(100, seed=1)
     tau = sig = 0.9 / nrm
     s.set_steps(tau, sig)
@@ -336,6 +338,8 @@ def run_ours(args):
     barrier()
     t0 = time.perf_counter()
     with Solver(Pp, precision=wl["precision"], stream=stream) as s2:
+        if args.precondition:
+            s2.set_scaling(10, True)
         nrm2 = s2.estimate_norm(100, seed=1)
         s2.set_steps(0.9 / nrm2, 0.9 / nrm2)
         s2.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
@@ -356,7 +360,7 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(P, wl, tau, sig, args.workload)
+        cpu = cpu_baseline(P, wl, tau, sig, args.workload, precondition=args.precondition)
 
     if rank == 0:
         line = {
@@ -366,7 +370,8 @@ def run_ours(args):
             "dtype": "f32+f64" if wl["precision"] == "mixed" else "f64",
             "data": "synthetic (seeded generator, known optimum; one LP per rank)",
             "config": {"workload": args.workload, "desc": wl["desc"], "m": P.m, "n": P.n,
-                       "nnz": P.nnz, "scale": args.scale, "memory": M, "method": wl["method"],
+                       "nnz": P.nnz, "scale": args.scale, "memory": M,
+                       "preconditioning": "Ruiz x10 + Pock-Chambolle" if args.precondition else "none", "method": wl["method"],
                        "precision": wl["precision"], "kkt_every": kkt_every,
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (no flush)" if P.nnz * 16 > 129e6 else
@@ -401,11 +406,13 @@ def kernel_source_hash(kind):
     return h.hexdigest()[:12]
 
 
-def cpu_baseline(P, wl, tau, sig, workload, budget_s=20.0):
+def cpu_baseline(P, wl, tau, sig, workload, budget_s=20.0, precondition=False):
     """The FP64 oracle as it stands, single-threaded, on the same LP: S AA-PDHG
     iterations timed end to end (including its one initial T application)."""
     from oracle import oracle as O
     lp = O.OracleLP.from_problem(P)
+    if precondition:
+        lp = O.scaled_lp(lp, *O.scaling(lp, 10, True))
     prm = O.Params(method={"aa": 1, "faa": 2, "pdhg": 0}[wl["method"]], mem=wl["mem"], tau=tau,
                    sigma=sig, D=10.0, eps=1.0)
     t0 = time.perf_counter()
@@ -458,6 +465,8 @@ def main():
     ap.add_argument("--ttt", action="store_true",
                     help="also time AA-PDHG and plain PDHG to KKT <= 1e-4 (KKT every 64 iterations)")
     ap.add_argument("--ttt-max-iters", type=int, default=200000)
+    ap.add_argument("--precondition", action="store_true",
+                    help="Ruiz (10 passes) + Pock-Chambolle diagonal scaling before the step size")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload's m, n, nnz (profiling captures only)")
     args = ap.parse_args()

@@ -123,6 +123,21 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
                                 double eta, double beta, double c_s, double kappa, double c_div,
                                 int32_t dhat_mode, int32_t faa_adaptive);
 
+/* Diagonal preconditioning of the LP, the set-up of the paper's comparison
+ * with restarted PDHG (Sec. 5.2: Ruiz scaling for 10 iterations combined with
+ * the Pock-Chambolle technique).  Each of the ruiz_iters passes divides every
+ * row and every column of the current scaled K by the square root of its
+ * largest |entry|; pock_chambolle != 0 adds one pass that divides them by the
+ * square root of their sum of |entries| (alpha = 1).  Empty rows and columns
+ * keep factor 1.  With the products Dr (rows) and Dc (columns) the solver then
+ * iterates on Dr K Dc, Dr q, Dc c and the bounds divided by Dc; start points
+ * (aapdhg_set_start), iterates (aapdhg_get_iterate: x = Dc x~, y = Dr y~) and
+ * the KKT quantities stay in the caller's units.  D-hat is formed from the
+ * scaled K.  Runs on the device; may be applied once per handle
+ * (AAPDHG_ERR_INVALID otherwise, or for ruiz_iters outside 0..1000); resets
+ * the run.  Step sizes are the caller's: estimate them after scaling.        */
+aapdhg_status aapdhg_set_scaling(aapdhg_t h, int32_t ruiz_iters, int32_t pock_chambolle);
+
 /* Start point u^0 = (x0, y0) (host arrays of n and m doubles, or NULL for the
  * default x0 = P_X(0), y0 = 0).  The start is projected onto X x Y, as Alg. 2
  * asks for a feasible start.  Resets the run.                                 */

@@ -37,6 +37,13 @@
  *  R8  FAA memory: adaptive mode (faa_adaptive = 1, the implemented variant of
  *      Sec. 5) replaces the memory by the filtered columns after every
  *      accepted AA step; literal mode filters a copy.
+ *  R12 Preconditioning (Sec. 5.2: Ruiz scaling for 10 iterations combined with
+ *      the Pock-Chambolle technique): each Ruiz pass divides every row and
+ *      every column of the current scaled K by the square root of its
+ *      largest |entry| (both from the same matrix; an empty row or column
+ *      keeps factor 1); the Pock-Chambolle pass (alpha = 1) then divides them
+ *      by the square root of their sum of |entries|.  The scaled LP is
+ *      Dr K Dc, Dr q, Dc c, bounds / Dc, with x = Dc x~ and y = Dr y~.
  */
 #include <math.h>
 #include <stdint.h>
@@ -124,6 +131,37 @@ void orc_dhat(const orc_lp *lp, int32_t mode, double *dx, double *dy) {
         }
     for (int32_t j = 0; j < lp->n; ++j) dx[j] = sqrt(fmax(dx[j], 1e-10));
     for (int32_t i = 0; i < lp->m; ++i) dy[i] = sqrt(fmax(dy[i], 1e-10));
+}
+
+/* ------------------------------------------------------------------------ */
+/* Diagonal preconditioning factors (reading R12): dr (m), dc (n).           */
+/* ------------------------------------------------------------------------ */
+static void scaled_row_col(const orc_lp *lp, const double *dr, const double *dc, int sum,
+                           double *rn, double *cn) {
+    for (int32_t i = 0; i < lp->m; ++i) rn[i] = 0.0;
+    for (int32_t j = 0; j < lp->n; ++j) cn[j] = 0.0;
+    for (int32_t i = 0; i < lp->m; ++i)
+        for (int64_t p = lp->rp[i]; p < lp->rp[i + 1]; ++p) {
+            const int32_t j = lp->ci[p];
+            const double a = fabs(dr[i] * lp->v[p] * dc[j]);
+            if (sum) { rn[i] += a; cn[j] += a; }
+            else { if (a > rn[i]) rn[i] = a; if (a > cn[j]) cn[j] = a; }
+        }
+}
+
+void orc_scaling(const orc_lp *lp, int32_t ruiz_iters, int32_t pock_chambolle, double *dr,
+                 double *dc) {
+    double *rn = calloc(lp->m > 0 ? lp->m : 1, sizeof(double));
+    double *cn = calloc(lp->n > 0 ? lp->n : 1, sizeof(double));
+    for (int32_t i = 0; i < lp->m; ++i) dr[i] = 1.0;
+    for (int32_t j = 0; j < lp->n; ++j) dc[j] = 1.0;
+    for (int32_t pass = 0; pass < ruiz_iters + (pock_chambolle ? 1 : 0); ++pass) {
+        const int sum = pass >= ruiz_iters;      /* the last pass is Pock-Chambolle */
+        scaled_row_col(lp, dr, dc, sum, rn, cn);
+        for (int32_t i = 0; i < lp->m; ++i) if (rn[i] > 0.0) dr[i] /= sqrt(rn[i]);
+        for (int32_t j = 0; j < lp->n; ++j) if (cn[j] > 0.0) dc[j] /= sqrt(cn[j]);
+    }
+    free(rn); free(cn);
 }
 
 /* ------------------------------------------------------------------------ */

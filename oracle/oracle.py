@@ -66,6 +66,7 @@ def lib():
         L.orc_solve.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_double, C.c_int32, vp, vp, vp,
                                 C.c_int64, vp, vp, vp, vp, C.c_int64, vp]
         L.orc_solve.restype = C.c_int
+        L.orc_scaling.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
         _lib = L
     return _lib
 
@@ -128,6 +129,20 @@ def dhat(lp: OracleLP, mode: int = 1):
     dx = np.empty(lp.n); dy = np.empty(lp.m)
     lib().orc_dhat(lp.ref, mode, _p(dx), _p(dy))
     return dx, dy
+
+
+def scaling(lp: OracleLP, ruiz_iters: int = 10, pock_chambolle: bool = True):
+    """Row and column factors (dr, dc) of the preconditioning (reading R12)."""
+    dr = np.empty(lp.m); dc = np.empty(lp.n)
+    lib().orc_scaling(lp.ref, int(ruiz_iters), int(bool(pock_chambolle)), _p(dr), _p(dc))
+    return dr, dc
+
+
+def scaled_lp(lp: OracleLP, dr, dc) -> OracleLP:
+    """The scaled LP: Dr K Dc, Dr q, Dc c, bounds / Dc (x = Dc x~, y = Dr y~)."""
+    rows = np.repeat(np.arange(lp.m), np.diff(lp.rp))
+    return OracleLP(lp.m, lp.n, lp.rp, lp.ci, dr[rows] * lp.v * dc[lp.ci], lp.sense, dr * lp.q,
+                    dc * lp.c, lp.l / dc, lp.u / dc)
 
 
 def T(lp: OracleLP, tau, sigma, x, y):

@@ -28,7 +28,8 @@ PRECISIONS = {"fp64": FP64, "mixed": MIXED}
 
 # every entry point declared in include/aapdhg.h
 EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_estimate_norm",
-           "aapdhg_set_method", "aapdhg_set_start", "aapdhg_reset", "aapdhg_iterate",
+           "aapdhg_set_method", "aapdhg_set_scaling", "aapdhg_set_start", "aapdhg_reset",
+           "aapdhg_iterate",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
            "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
@@ -61,6 +62,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_set_steps.argtypes = [vp, f64, f64]
     L.aapdhg_estimate_norm.argtypes = [vp, i32, C.c_uint64, C.POINTER(f64)]
     L.aapdhg_set_method.argtypes = [vp, i32, i32, f64, f64, f64, f64, f64, f64, f64, i32, i32]
+    L.aapdhg_set_scaling.argtypes = [vp, i32, i32]
     L.aapdhg_set_start.argtypes = [vp, vp, vp]
     L.aapdhg_reset.argtypes = [vp]
     L.aapdhg_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
@@ -199,6 +201,10 @@ class Solver:
         m = METHODS[method] if isinstance(method, str) else int(method)
         self._check(self._L.aapdhg_set_method(self._h, m, int(mem), D, eps, eta, beta, c_s,
                                               kappa, c_div, int(dhat_mode), int(faa_adaptive)))
+
+    def set_scaling(self, ruiz_iters=10, pock_chambolle=True):
+        """Ruiz + Pock-Chambolle diagonal scaling (once per solver; resets the run)."""
+        self._check(self._L.aapdhg_set_scaling(self._h, int(ruiz_iters), int(bool(pock_chambolle))))
 
     def set_start(self, x0=None, y0=None):
         x0 = None if x0 is None else _f64(x0, self.n)

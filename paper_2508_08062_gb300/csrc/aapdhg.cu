@@ -19,6 +19,7 @@
 #include "../../include/aapdhg.h"
 #include "anderson.cuh"
 #include "common.cuh"
+#include "precond.cuh"
 #include "spmv.cuh"
 
 using namespace aap;
@@ -142,6 +143,8 @@ struct aapdhg_s {
     std::vector<GraphEntry> graphs;
     bool use_graphs = true;
     int32_t dhat_mode = -1;                // mode D-hat was last formed with
+    bool scaled = false;                   // aapdhg_set_scaling applied
+    std::vector<double> dr_host, dc_host;  // Dr, Dc in internal order (when scaled)
     // raw device pointers kept for re-initialisation
     void *d_UP = nullptr;
     void *d_lo = nullptr;
@@ -438,6 +441,7 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     if (!ok) return fail(h, AAPDHG_ERR_OOM, "device allocation or copy failed during create");
     CK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
     P.DG = P.W = nullptr;
+    P.sc_x = P.sc_y = nullptr;
     P.tr = Trace{0, nullptr, nullptr, nullptr, nullptr};
 
     // D-hat and the norms ||q||, ||c|| on the device
@@ -474,12 +478,12 @@ template <typename V> aapdhg_status reset_run(aapdhg_t h) {
     std::vector<V2> up(h->N);
     for (int32_t j = 0; j < n; ++j) {
         const int32_t oj = h->perm_x[j];
-        up[j].x = (V)h->x0[oj];
+        up[j].x = (V)(h->scaled ? h->x0[oj] / h->dc_host[j] : h->x0[oj]);
         up[j].y = V(0);
     }
     for (int32_t i = 0; i < m; ++i) {
         const int32_t oi = h->perm_y[i];
-        up[n + i].x = (V)h->y0[oi];
+        up[n + i].x = (V)(h->scaled ? h->y0[oi] / h->dr_host[i] : h->y0[oi]);
         up[n + i].y = V(0);
     }
     CK(h, cudaMemcpyAsync(P.UP, up.data(), sizeof(V2) * h->N, cudaMemcpyHostToDevice, h->stream));
@@ -665,10 +669,15 @@ template <typename V> aapdhg_status get_iterate_t(aapdhg_t h, double *x, double 
     CK(h, cudaMemcpyAsync(up.data(), P.UP, sizeof(V2) * h->N, cudaMemcpyDeviceToHost, h->stream));
     CK(h, cudaStreamSynchronize(h->stream));
     if (x)
-        for (int32_t j = 0; j < h->n; ++j) x[h->perm_x[j]] = (double)(cur ? up[j].y : up[j].x);
+        for (int32_t j = 0; j < h->n; ++j) {
+            const double v = (double)(cur ? up[j].y : up[j].x);
+            x[h->perm_x[j]] = h->scaled ? v * h->dc_host[j] : v;      // x = Dc x~
+        }
     if (y)
-        for (int32_t i = 0; i < h->m; ++i)
-            y[h->perm_y[i]] = (double)(cur ? up[h->n + i].y : up[h->n + i].x);
+        for (int32_t i = 0; i < h->m; ++i) {
+            const double v = (double)(cur ? up[h->n + i].y : up[h->n + i].x);
+            y[h->perm_y[i]] = h->scaled ? v * h->dr_host[i] : v;      // y = Dr y~
+        }
     return AAPDHG_OK;
 }
 
@@ -723,6 +732,56 @@ template <typename V> aapdhg_status estimate_norm_t(aapdhg_t h, int32_t iters, u
         if (g_free) g_free(a.p, g_ctx); else cudaFree(a.p);
     }
     *norm = sqrt(lam);
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status set_scaling_t(aapdhg_t h, int32_t ruiz_iters, int32_t pc) {
+    Prob<V> &P = prob<V>(h);
+    const int32_t m = h->m, n = h->n;
+    V *dr = (V *)dev_alloc(h, sizeof(V) * std::max(m, 1));
+    V *dc = (V *)dev_alloc(h, sizeof(V) * n);
+    V *tr = (V *)dev_alloc(h, sizeof(V) * std::max(m, 1));
+    V *tc = (V *)dev_alloc(h, sizeof(V) * n);
+    V *scx = (V *)dev_alloc(h, sizeof(V) * n);
+    V *scy = (V *)dev_alloc(h, sizeof(V) * std::max(m, 1));
+    if (!dr || !dc || !tr || !tc || !scx || !scy) return fail(h, AAPDHG_ERR_OOM, "scaling buffers");
+    cudaStream_t s = h->stream;
+    const int gv = grid_for(h, (h->N + BLOCK - 1) / BLOCK, 4);
+    const int gr = grid_for(h, (h->N + WARPS - 1) / WARPS, 8);
+    k_fill<V><<<gv, BLOCK, 0, s>>>(dr, V(1), m);
+    k_fill<V><<<gv, BLOCK, 0, s>>>(dc, V(1), n);
+    for (int32_t pass = 0; pass < ruiz_iters + (pc ? 1 : 0); ++pass) {
+        const int sum = pass >= ruiz_iters;          // the last pass is Pock-Chambolle
+        if (m > 0) k_row_norm<V><<<gr, BLOCK, 0, s>>>(P.K, sum, tr);
+        k_row_norm<V><<<gr, BLOCK, 0, s>>>(P.KT, sum, tc);
+        k_factor<V><<<gv, BLOCK, 0, s>>>(tr, m);
+        k_factor<V><<<gv, BLOCK, 0, s>>>(tc, n);
+        if (m > 0) k_scale_matrix<V><<<gr, BLOCK, 0, s>>>(P.K, tr, tc);
+        k_scale_matrix<V><<<gr, BLOCK, 0, s>>>(P.KT, tc, tr);
+        k_vmul<V><<<gv, BLOCK, 0, s>>>(dr, tr, m);
+        k_vmul<V><<<gv, BLOCK, 0, s>>>(dc, tc, n);
+    }
+    k_vmul<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.c), dc, n);
+    k_vmul<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.q), dr, m);
+    k_vdiv<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.lo), dc, n);   // x part of the bounds
+    k_vdiv<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.hi), dc, n);
+    k_vinv<V><<<gv, BLOCK, 0, s>>>(scx, dc, n);
+    k_vinv<V><<<gv, BLOCK, 0, s>>>(scy, dr, m);
+    CK(h, cudaGetLastError());
+    std::vector<V> hr(std::max(m, 1)), hc(n);
+    CK(h, cudaMemcpyAsync(hr.data(), dr, sizeof(V) * m, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaMemcpyAsync(hc.data(), dc, sizeof(V) * n, cudaMemcpyDeviceToHost, s));
+    CK(h, cudaStreamSynchronize(s));
+    h->dr_host.assign(hr.begin(), hr.begin() + m);
+    h->dc_host.assign(hc.begin(), hc.end());
+    P.sc_x = scx;
+    P.sc_y = m > 0 ? scy : nullptr;
+    // D-hat of the scaled K
+    const int gD = grid_for(h, (h->N + WARPS - 1) / WARPS, 8);
+    k_dhat<V><<<gD, BLOCK, 0, s>>>(P.KT, P.K, n, m, h->dhat_mode < 0 ? 1 : h->dhat_mode,
+                                   const_cast<V *>(P.dh));
+    CK(h, cudaGetLastError());
+    h->scaled = true;
     return AAPDHG_OK;
 }
 
@@ -900,6 +959,18 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
         CK(h, cudaGetLastError());
         h->dhat_mode = dhat_mode;
     }
+    return reset_any(h);
+}
+
+aapdhg_status aapdhg_set_scaling(aapdhg_t h, int32_t ruiz_iters, int32_t pock_chambolle) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (h->scaled || ruiz_iters < 0 || ruiz_iters > 1000)
+        return fail(h, AAPDHG_ERR_INVALID, "scaling is applied at most once, with 0..1000 Ruiz passes");
+    drop_graphs(h);
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? set_scaling_t<double>(h, ruiz_iters, pock_chambolle)
+                                             : set_scaling_t<float>(h, ruiz_iters, pock_chambolle);
+    if (s != AAPDHG_OK) return s;
     return reset_any(h);
 }
 

@@ -166,6 +166,7 @@ template <typename V> struct Prob {
     const V *dh;                  // N: D-hat
     V *g;                         // N: g^{k-1} / g^k
     V *DG, *W;                    // NSLOT * Npad rings: dg and du + beta D dg
+    const V *sc_x, *sc_y;         // 1 / Dc (n) and 1 / Dr (m) when the LP is scaled, else null
     double *part1, *part2, *part3;// block partials of the x-step, y-step, memory pass
     int32_t grid1, grid2, grid3;  // grids of those kernels (fixed: deterministic sums)
     DevState *st;

@@ -1,0 +1,95 @@
+// Diagonal preconditioning of the LP on the device (the Sec. 5.2 set-up:
+// Ruiz scaling for 10 iterations combined with the Pock-Chambolle technique).
+//
+// A pass computes, from the current scaled K, one factor per row and one per
+// column, 1 / sqrt(norm) (Ruiz: largest |entry|; Pock-Chambolle, alpha = 1:
+// sum of |entries|; an empty row or column keeps 1), and multiplies every
+// stored copy of K (CSR and SELL slices) and of K' by them.  The products of
+// the factors are Dr (rows) and Dc (columns); the solver then iterates on
+// Dr K Dc, Dr q, Dc c and the bounds divided by Dc.
+#pragma once
+#include "common.cuh"
+
+namespace aap {
+
+// out[r] = max_k |A_rk| (sum = 0) or sum_k |A_rk| (sum = 1); one warp per row.
+template <typename V>
+__global__ void k_row_norm(CSRView<V> A, int sum, V *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < A.rows;
+         r += warps) {
+        V acc = V(0);
+        for (int k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) {
+            const V a = fabs(A.val[k]);
+            acc = sum ? acc + a : fmax(acc, a);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            const V b = __shfl_xor_sync(0xffffffffu, acc, o);
+            acc = sum ? acc + b : fmax(acc, b);
+        }
+        if (lane == 0) out[r] = acc;
+    }
+}
+
+// d <- 1 / sqrt(d) where d > 0, else 1.
+template <typename V>
+__global__ void k_factor(V *d, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        d[i] = d[i] > V(0) ? V(1) / sqrt(d[i]) : V(1);
+}
+
+// A_rk <- A_rk * drow[r] * dcol[col(k)] for the CSR copy (one warp per row)
+// and for the SELL slices (one warp per slice, lane = row).
+template <typename V>
+__global__ void k_scale_matrix(CSRView<V> A, const V *drow, const V *dcol) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    V *val = const_cast<V *>(A.val);
+    for (int64_t r = w0; r < A.rows; r += warps) {
+        const V fr = drow[r];
+        for (int k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) val[k] = val[k] * fr * dcol[A.ci[k]];
+    }
+    V *sv = const_cast<V *>(A.sell_val);
+    for (int64_t s = w0; s < A.n_slices; s += warps) {
+        const int2 meta = A.slice_meta[s];
+        const int64_t r = A.n_long + s * 32 + lane;
+        if (r >= A.rows) continue;
+        const V fr = drow[r];
+        for (int t = 0; t < meta.y; ++t) {
+            const int64_t q = (int64_t)meta.x + (int64_t)t * 32 + lane;
+            sv[q] = sv[q] * fr * dcol[A.sell_ci[q]];    // padding entries are 0 and stay 0
+        }
+    }
+}
+
+// Elementwise helpers: a *= b, a /= b, out = 1 / b, a = v.
+template <typename V>
+__global__ void k_vmul(V *a, const V *b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] *= b[i];
+}
+template <typename V>
+__global__ void k_vdiv(V *a, const V *b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] /= b[i];
+}
+template <typename V>
+__global__ void k_vinv(V *out, const V *b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = V(1) / b[i];
+}
+template <typename V>
+__global__ void k_fill(V *a, V v, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+}  // namespace aap

@@ -176,7 +176,10 @@ template <typename V, bool KKT> struct EpiX {
             else if (!lf) lamj = r < V(0) ? r : V(0);
             else if (!uf) lamj = r > V(0) ? r : V(0);
             else lamj = r;
-            dres2.add_sq(r - lamj);
+            // residual in the caller's units: (c - K'y - lambda)_j = (scaled) / Dc_j
+            V d = r - lamj;
+            if (P.sc_x) d *= __ldg(P.sc_x + j);
+            dres2.add_sq(d);
             if (lamj > V(0)) lam.add_prod(l, lamj);         // l' lambda+
             else if (lamj < V(0)) lam.add_prod(u, lamj);    // - u' lambda-
             cx.add_prod(cj, x);
@@ -239,6 +242,7 @@ template <typename V, bool KKT> struct EpiY {
         if (KKT) {
             V p = qi - t[1];                        // q - K x^k
             if (l == V(0) && p < V(0)) p = V(0);    // '>=' rows: only violation counts
+            if (P.sc_y) p *= __ldg(P.sc_y + i);     // caller's units: (q - Kx)_i = (scaled) / Dr_i
             pres2.add_sq(p);
             qy.add_prod(qi, y);
         }

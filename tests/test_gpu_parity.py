@@ -242,3 +242,55 @@ def test_invalid_inputs_rejected():
     with _solver(P) as s:
         with pytest.raises(AAPDHGError):
             s.set_method("aa", mem=33)
+
+
+# --------------------------------------------------------------------------
+# Diagonal preconditioning (Ruiz x10 + Pock-Chambolle, the Sec. 5.2 set-up)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("method", [1, 2])
+def test_fp64_scaled_iterates_match_oracle(method):
+    P = lpgen.random_lp(300, 650, nnz_per_row=6, frac_ge=0.4, frac_free=0.15, frac_lower_only=0.1,
+                        frac_upper_only=0.1, row_scale_sigma=2.0, seed=17)
+    lp = O.OracleLP.from_problem(P)
+    dr, dc = O.scaling(lp, 10, True)
+    S = O.scaled_lp(lp, dr, dc)
+    from scipy.sparse.linalg import svds
+    Ks = sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n))
+    tau = sig = 0.9 / svds(Ks, k=1, return_singular_vectors=False, random_state=0)[0]
+    prm = O.Params(method=method, mem=6, tau=tau, sigma=sig)
+    ref = O.solve(S, prm, ITERS, trace=True, rec_len=ITERS + 1)
+    with _solver(P) as s:
+        s.set_scaling(10, True)
+        s.set_steps(tau, sig)
+        s.set_method(method=method, mem=6)
+        s.set_trace(ITERS)
+        s.iterate(0)
+        for k in range(ITERS + 1):
+            x, y = s.get_iterate()
+            r = np.concatenate([dc * ref.rec_u[k][:P.n], dr * ref.rec_u[k][P.n:]])
+            err = np.linalg.norm(np.concatenate([x, y]) - r) / np.linalg.norm(r)
+            assert err <= FP64_TOL, (k, err)
+            if k < ITERS:
+                s.iterate(1)
+        tr = s.get_trace()
+        g = s.get_kkt()
+    assert np.array_equal(tr["branch"][:ITERS], ref.branch[:ITERS])
+    o = O.kkt(lp, x, y)                       # KKT in the caller's (unscaled) units
+    for k in ("r_p", "r_d", "r_g", "kkt", "pobj", "dobj"):
+        assert abs(g[k] - o[k]) <= 1e-10 * (abs(o[k]) + 1e-6), (k, g[k], o[k])
+
+
+def test_scaling_only_once_and_start_in_caller_units():
+    from paper_2508_08062_gb300 import AAPDHGError
+    P = lpgen.random_lp(50, 80, row_scale_sigma=2.0, seed=2)
+    rng = np.random.default_rng(0)
+    x0 = np.clip(rng.standard_normal(P.n), P.l, P.u)
+    y0 = np.abs(rng.standard_normal(P.m))
+    with _solver(P) as s:
+        s.set_scaling(10, True)
+        s.set_steps(0.1, 0.1)
+        s.set_start(x0, y0)
+        x, y = s.get_iterate()
+        assert np.allclose(x, x0, rtol=1e-14) and np.allclose(y, y0, rtol=1e-14)
+        with pytest.raises(AAPDHGError):
+            s.set_scaling(10, True)

@@ -552,3 +552,47 @@ def test_faa_adaptive_memory_shrinks():
     used = r.mk[r.branch == 1]
     assert used.size > 0 and used.max() <= 5
     assert (used < 5).any()   # filtering dropped columns at least once
+
+
+# --------------------------------------------------------------------------
+# Preconditioning (Sec. 5.2 set-up: Ruiz x10 + Pock-Chambolle, reading R12)
+# --------------------------------------------------------------------------
+def test_pock_chambolle_by_hand():
+    # K = [[4, 0], [1, 9]]: row sums 4, 10; column sums 5, 9
+    P = lpgen.from_dense([[4.0, 0.0], [1.0, 9.0]], [0, 0], [1, 1], [1, 1], [0, 0], [1, 1])
+    dr, dc = O.scaling(O.OracleLP.from_problem(P), 0, True)
+    assert np.allclose(dr, [0.5, 1 / np.sqrt(10)], rtol=1e-15)
+    assert np.allclose(dc, [1 / np.sqrt(5), 1 / 3], rtol=1e-15)
+
+
+def test_ruiz_equilibrates_inf_norms():
+    P = lpgen.random_lp(60, 90, nnz_per_row=6, row_scale_sigma=3.0, seed=4)
+    lp = O.OracleLP.from_problem(P)
+    dr, dc = O.scaling(lp, 40, False)
+    S = O.scaled_lp(lp, dr, dc)
+    import scipy.sparse as sp
+    A = abs(sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n)))
+    rmax = A.max(axis=1).toarray().ravel()
+    cmax = A.max(axis=0).toarray().ravel()
+    assert np.max(np.abs(rmax[rmax > 0] - 1)) < 1e-3
+    assert np.max(np.abs(cmax[cmax > 0] - 1)) < 1e-3
+
+
+def test_scaled_lp_has_the_same_solution():
+    P = lpgen.random_lp(40, 70, nnz_per_row=5, frac_ge=0.4, frac_free=0.1,
+                        frac_lower_only=0.1, frac_upper_only=0.1, row_scale_sigma=2.0, seed=8)
+    lp = O.OracleLP.from_problem(P)
+    dr, dc = O.scaling(lp, 10, True)
+    S = O.scaled_lp(lp, dr, dc)
+    # the constructed optimum maps to an optimum of the scaled LP
+    k = O.kkt(S, P.x_star / dc, P.y_star / dr)
+    assert k["r_p"] < 1e-12 and k["r_d"] < 1e-12 and abs(k["pobj"] - P.pobj_star) < 1e-9
+    # and solving the scaled LP gives the original optimum back
+    import scipy.sparse as sp
+    A = sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n)).toarray()
+    step = 0.9 / np.linalg.norm(A, 2)
+    r = O.solve(S, O.Params(method=1, mem=5, tau=step, sigma=step), 300000, tol=3e-5, kkt_every=10)
+    assert r.status == 0
+    x = dc * r.x
+    assert abs(P.c @ x - P.pobj_star) <= 1e-3 * (1 + abs(P.pobj_star))
+    assert O.kkt(lp, x, dr * r.y)["kkt"] < 1e-3

@@ -50,6 +50,12 @@ WORKLOADS = {
                         "with 10% free; AA-PDHG m=10, mixed precision"),
     "tiny": dict(method="aa", mem=5, precision="fp64",
                  desc="200 x 500 CSR, 10 nnz/row, N(0,1), '=' rows, 0<=x<=10; AA-PDHG m=5, FP64"),
+    "batch": dict(method="aa", mem=10, precision="mixed",
+                  desc="256 independent LPs, rows log-uniform in [1k, 50k], cols 2.5x rows, "
+                       "lognormal row lengths (mean 8), N(0,1)*lognormal(0,2) per row, 30% '>=' "
+                       "rows, bounds [0,U(1,100)] with 10% free; packed block-diagonal, Ruiz x10 + "
+                       "Pock-Chambolle per LP, AA-PDHG m=10 mixed precision, solved to 1e-4 "
+                       "relative KKT (tested every 64 iterations)"),
 }
 
 
@@ -427,10 +433,280 @@ def cpu_baseline(P, wl, tau, sig, workload, budget_s=20.0, precondition=False):
                       f"{workload} LP from its start (includes the initial T), 1 thread"}
 
 
+def run_batch(args):
+    """The batched workload: solves/s at 1e-4 relative KKT of the packed batch,
+    against FP64 single-LP AA-PDHG solving the same LPs one at a time."""
+    import torch
+    import torch.distributed as dist
+    import lpgen
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2508_08062_gb300 import BatchSolver, Solver
+
+    wl = WORKLOADS["batch"]
+    M, kkt_every, tol = wl["mem"], 64, 1e-4
+    members = lpgen.batch(seed=lpgen.SEED_BASE + 4 + 1000 * rank, scale=args.scale)
+    nprob = len(members)
+    Ztot = sum(P.nnz for P in members)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def prepare(b):
+        b.set_scaling(10, True)
+        nrm = b.estimate_norms(100, seed=1)
+        b.set_steps(0.9 / nrm, 0.9 / nrm)
+        b.set_method("aa", mem=M, D=10.0, eps=1.0)
+
+    b = BatchSolver(members, precision="mixed", stream=stream)
+    prepare(b)
+    dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
+    dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(dev_id) as clk:
+        b.iterate(max(args.warmup, 3) * kkt_every, tol=tol, kkt_every=kkt_every)   # graphs, clocks
+        b.reset()
+        l0 = b.launch_count()
+        barrier()
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        done_at = np.full(nprob, np.nan)
+        its = 0
+        while its < args.batch_max_iters:
+            conv, n = b.iterate(kkt_every, tol=tol, kkt_every=kkt_every)
+            its += n
+            st = b.status()
+            now = time.perf_counter() - t0
+            done_at[(st[:, 4] == 1) & np.isnan(done_at)] = now
+            if conv or n == 0:
+                break
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    launches = b.launch_count() - l0
+    st = b.status()
+    solved = int(st[:, 4].sum())
+    t_max = ms
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * solved / (t_max / 1e3)
+    kk = b.get_kkt()
+
+    # throughput with every member active (tol = 0) and the roofline
+    b.reset()
+    b.iterate(kkt_every, tol=0.0, kkt_every=kkt_every)
+    b.profile_kernels(True)
+    b.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+    prof = b.kernel_profile()
+    b.profile_kernels(False)
+    barrier()
+    ev0.record(stream)
+    b.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
+    ev1.record(stream)
+    barrier()
+    thr_ms = ev0.elapsed_time(ev1)
+    st2 = b.status()
+    peak, peak_src = measured_peak()
+
+    class _Packed:   # the packed LP's sizes for the per-kernel byte formulas
+        pass
+    PK = _Packed()
+    PK.n = sum((P.n + 3) // 4 * 4 for P in members)
+    PK.m = sum((P.m + 3) // 4 * 4 for P in members)
+    PK.nnz = Ztot
+    acc = int(st2[:, 1].sum())
+    kern = {}
+    for kind, d in prof.items():
+        if not d["launches"] or kind == "kkt":
+            continue
+        bts = kernel_bytes(PK, 4, kind, M, d["launches"], 0, 0, 0) if kind != "mix" else None
+        gbs = bts / (d["total_ms"] / 1e3) / 1e9 if bts else None
+        kern[kind] = dict(launches=d["launches"], avg_us=1e3 * d["total_ms"] / d["launches"],
+                          alg_bytes_per_launch=(bts / d["launches"]) if bts else None, gbs=gbs,
+                          frac_of_measured_hbm=(gbs / peak) if gbs else None)
+    tot = sum(d["total_ms"] for d in prof.values())
+    for kind in kern:
+        kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
+    dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: prof[k]["total_ms"])
+    roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
+                "frac": kern[dom]["frac_of_measured_hbm"], "traffic": None, "kernel": dom,
+                "peak_source": peak_src, "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"]}
+    b.close()
+
+    # end to end through the public API: create from host arrays, scaling,
+    # step sizes, solve to 1e-4, read every x, y back
+    barrier()
+    t0 = time.perf_counter()
+    with BatchSolver(members, precision="mixed", stream=stream) as b2:
+        prepare(b2)
+        conv2, its2 = b2.iterate(args.batch_max_iters, tol=tol, kkt_every=kkt_every)
+        solved2 = int(b2.status()[:, 4].sum())
+        b2.get_iterate()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * solved2 / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": sum(problem_bytes(P) for P in members) / max(its2, 1),
+           "d2h_bytes_per_step": (8 * sum(P.n + P.m for P in members)) / max(its2, 1),
+           "session": "create from host CSR of 256 LPs (validation, renumbering, packing, H2D) "
+                      "+ scaling + 100 power iterations + solve to 1e-4 + x,y read back"}
+
+    # baseline: FP64 single-LP AA-PDHG, one LP at a time, on a stratified sample
+    single = None
+    if args.single_sample > 0:
+        order = np.argsort([P.m for P in members])
+        pick = order[np.linspace(0, nprob - 1, min(args.single_sample, nprob)).astype(int)]
+        times, iters, ok = [], [], 0
+        for p in pick:
+            with Solver(members[p], precision="fp64", stream=stream) as s:
+                s.set_scaling(10, True)
+                nrm = s.estimate_norm(100, seed=1)
+                s.set_steps(0.9 / nrm, 0.9 / nrm)
+                s.set_method("aa", mem=M, D=10.0, eps=1.0)
+                barrier()
+                t0 = time.perf_counter()
+                c, n = s.iterate(args.batch_max_iters, tol=tol, kkt_every=kkt_every)
+                barrier()
+                times.append(time.perf_counter() - t0)
+                iters.append(n)
+                ok += int(c)
+        est = float(np.sum(times)) * nprob / len(pick)
+        single = {"solves_per_s": nprob / est, "sample": [int(p) for p in pick],
+                  "sample_rows": [int(members[p].m) for p in pick],
+                  "sample_seconds": [round(t, 4) for t in times], "sample_iterations": iters,
+                  "sample_converged": ok, "estimated_seconds_all": est,
+                  "note": "FP64 single-LP solver (same scaling, step rule, AA m=10, KKT every 64), "
+                          "solve time per LP, stratified by size; total = mean x 256"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_batch(members, st, M)
+
+    if rank == 0:
+        fin = done_at[~np.isnan(done_at)]
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+            "steps": int(its), "warmup": max(args.warmup, 3) * kkt_every,
+            "ms_per_step": t_max / max(its, 1), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded generator, known optimum per LP; one batch per rank)",
+            "config": {"workload": "batch", "desc": wl["desc"], "nprob": nprob,
+                       "rows": int(sum(P.m for P in members)), "cols": int(sum(P.n for P in members)),
+                       "nnz": int(Ztot), "scale": args.scale, "memory": M, "kkt_every": kkt_every,
+                       "tol": tol, "parallelism": f"replicas{world}",
+                       "l2": "inputs larger than L2 (no flush)"},
+            "solved": solved, "batch_iterations": int(its),
+            "member_iterations": {"p50": float(np.median(st[:, 0])), "max": int(st[:, 0].max()),
+                                  "sum": int(st[:, 0].sum())},
+            "time_to_tol_s": {"p50": float(np.percentile(fin, 50)) if len(fin) else None,
+                              "p99": float(np.percentile(fin, 99)) if len(fin) else None,
+                              "note": "per LP, from the batch start, at 64-iteration granularity"},
+            "kkt_max": float(np.max(kk[:, 3])),
+            "throughput_all_active": {"batch_iters_per_s": args.steps / (thr_ms / 1e3),
+                                      "member_iters_per_s": nprob * args.steps / (thr_ms / 1e3)},
+            "roofline": roofline, "kernels": kern,
+            "single_lp_fp64_one_at_a_time": single,
+            "speedup_vs_single_fp64": (value / single["solves_per_s"]) if single else None,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline_batch(members, st, M, budget_s=20.0):
+    """The FP64 oracle as it stands on one median-size member of the batch
+    (scaled as the GPU run scales it), timed for a bounded number of AA-PDHG
+    iterations; solves/s of the batch are then estimated from the oracle's
+    time per iteration and nonzero (x each member's nonzeros) and the
+    iteration counts the GPU run needed per member."""
+    from oracle import oracle as O
+    from scipy.sparse.linalg import svds
+    import scipy.sparse as sp
+    order = np.argsort([P.m for P in members])
+    p = int(order[len(order) // 2])
+    P = members[p]
+    lp = O.OracleLP.from_problem(P)
+    S = O.scaled_lp(lp, *O.scaling(lp, 10, True))
+    K = sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n))
+    tau = 0.9 / svds(K, k=1, return_singular_vectors=False, random_state=0, maxiter=200, tol=1e-3)[0]
+    prm = O.Params(method=1, mem=M, tau=tau, sigma=tau, D=10.0, eps=1.0)
+    t0 = time.perf_counter()
+    O.solve(S, prm, 10)
+    t1 = (time.perf_counter() - t0) / 10
+    n_it = int(max(10, min(100000, budget_s / max(t1, 1e-7))))
+    t0 = time.perf_counter()
+    O.solve(S, prm, n_it)
+    per_it = (time.perf_counter() - t0) / n_it
+    per_nnz_it = per_it / max(P.nnz, 1)
+    est = sum(per_nnz_it * Q.nnz * max(int(st[q, 0]), 1) for q, Q in enumerate(members))
+    return {"value": len(members) / est, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n_it} FP64 oracle AA-PDHG iterations (m={M}) on batch member {p} "
+                      f"({P.m}x{P.n}, {P.nnz} nnz, scaled); batch time estimated as oracle "
+                      f"seconds per iteration per nonzero x each member's nonzeros x the "
+                      f"iterations it needed on the GPU"}
+
+
+def run_reference_batch(args):
+    """Reference arm of the batched workload: the FP64 oracle solving members
+    (stratified by size, smallest first) to 1e-4 until its time budget is
+    spent; solves/s normalised to the batch's mean nonzeros per LP."""
+    import lpgen
+    from oracle import oracle as O
+    from scipy.sparse.linalg import svds
+    import scipy.sparse as sp
+    members = lpgen.batch(scale=args.scale)
+    order = np.argsort([P.m for P in members])
+    pick = sorted(order[np.linspace(0, len(members) - 1, 16).astype(int)], key=lambda q: members[q].m)
+    budget = float(os.environ.get("REF_BUDGET_S", "120"))
+    t0 = time.perf_counter()
+    done, nnz_done = 0, 0
+    for q in pick:
+        P = members[q]
+        lp = O.OracleLP.from_problem(P)
+        S = O.scaled_lp(lp, *O.scaling(lp, 10, True))
+        K = sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n))
+        tau = 0.9 / svds(K, k=1, return_singular_vectors=False, random_state=0, maxiter=200,
+                         tol=1e-3)[0]
+        r = O.solve(S, O.Params(method=1, mem=10, tau=tau, sigma=tau), 100000, tol=1e-4,
+                    kkt_every=64)
+        if r.status != 0:
+            continue
+        done += 1
+        nnz_done += P.nnz
+        if time.perf_counter() - t0 > budget:
+            break
+    dt = time.perf_counter() - t0
+    mean_all = np.mean([P.nnz for P in members])
+    v = (done / dt) * ((nnz_done / max(done, 1)) / mean_all) if done else 0.0
+    sample = (f"{done} batch members (stratified by size, smallest first) solved to 1e-4 by the "
+              f"FP64 oracle in {dt:.1f} s, 1 thread; rate scaled by their mean nnz / the batch's")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": 1,
+            "steps": done, "warmup": 0, "ms_per_step": 1e3 * dt / max(done, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": "batch", "desc": WORKLOADS["batch"]["desc"]},
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
+    if args.workload == "batch":
+        return run_reference_batch(args)
     wl = WORKLOADS[args.workload]
     P = make_problem(args.workload, 0, args.scale)
     from scipy.sparse.linalg import svds
@@ -467,6 +743,10 @@ def main():
     ap.add_argument("--ttt-max-iters", type=int, default=200000)
     ap.add_argument("--precondition", action="store_true",
                     help="Ruiz (10 passes) + Pock-Chambolle diagonal scaling before the step size")
+    ap.add_argument("--batch-max-iters", type=int, default=100000,
+                    help="batch workload: iteration cap of the solve to 1e-4")
+    ap.add_argument("--single-sample", type=int, default=16,
+                    help="batch workload: LPs solved one at a time by the FP64 single-LP solver")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload's m, n, nnz (profiling captures only)")
     args = ap.parse_args()
@@ -474,6 +754,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

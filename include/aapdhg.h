@@ -248,6 +248,103 @@ const char *aapdhg_last_error(aapdhg_t h);
 /* Free the handle and its device memory (synchronises its stream).          */
 void aapdhg_destroy(aapdhg_t h);
 
+/* ===========================================================================
+ * Batched solver: many independent LPs advanced together on one GPU.
+ *
+ * The same method as above (PDHG step of eq. pdhg, Alg. 2 / Alg. 3 with the
+ * safeguard, the termination test of the Remark on termination conditions),
+ * applied to every LP of the batch at once; each LP has its own step sizes,
+ * Anderson memory, safeguard, iteration count and stop flag, and stops when
+ * its own KKT residual meets the tolerance.  The paper solves one LP at a
+ * time; the batch packs the LPs into one block-diagonal LP (padded so each
+ * problem's variable and constraint ranges start on 16-byte boundaries) and
+ * computes every row of T(u) exactly as the single-LP solver does for that LP.
+ * Method settings (aapdhg_batch_set_method) apply to all problems.
+ *
+ * Inputs of create are host memory, every per-problem array concatenated in
+ * problem order:
+ *   nprob                 number of LPs, 1 <= nprob < 2^25
+ *   m[p], n[p], nnz[p]    sizes of LP p (as in aapdhg_create)
+ *   row_ptr               sum(m[p] + 1) int64: each LP's own CSR row pointers
+ *                         (starting at 0)
+ *   col_idx, val          sum(nnz[p]): each LP's column indices (its own
+ *                         variable numbering) and values
+ *   row_sense, q          sum(m[p]);   c, lb, ub   sum(n[p])
+ * Each LP is validated as aapdhg_create does (the error message names the
+ * problem).  The packed batch must hold < 2^31 nonzeros and < 2^31 elements.
+ * The library copies everything; the caller keeps ownership.  Defaults, the
+ * allocator and the stream rules are those of aapdhg_create; the handle is
+ * used from one host thread at a time.  Errors are sticky as for aapdhg_t,
+ * except AAPDHG_ERR_NUMERIC from iterate, which reports that at least one LP
+ * stopped on NaN/Inf while the others went on (see aapdhg_batch_get_status). */
+typedef struct aapdhg_batch_s *aapdhg_batch_t;
+
+aapdhg_status aapdhg_batch_create(int32_t nprob, const int32_t *m, const int32_t *n,
+                                  const int64_t *nnz, const int64_t *row_ptr,
+                                  const int32_t *col_idx, const double *val,
+                                  const int8_t *row_sense, const double *q, const double *c,
+                                  const double *lb, const double *ub, int32_t precision,
+                                  void *cuda_stream, aapdhg_batch_t *out);
+
+/* Per-problem step sizes tau[p], sigma[p] (host arrays of nprob, finite, > 0);
+ * resets every problem to its start.                                         */
+aapdhg_status aapdhg_batch_set_steps(aapdhg_batch_t h, const double *tau, const double *sigma);
+
+/* Per-problem estimate of ||K_p||_2 by `iters` power iterations on K_p'K_p
+ * (Sec. 5.1), all problems at once; norms: host array of nprob.  For a given
+ * seed each problem starts from the vector the single-LP solver uses.        */
+aapdhg_status aapdhg_batch_estimate_norms(aapdhg_batch_t h, int32_t iters, uint64_t seed,
+                                          double *norms);
+
+/* As aapdhg_set_method, for every problem of the batch.                      */
+aapdhg_status aapdhg_batch_set_method(aapdhg_batch_t h, int32_t method, int32_t m_A, double D,
+                                      double eps, double eta, double beta, double c_s,
+                                      double kappa, double c_div, int32_t dhat_mode,
+                                      int32_t faa_adaptive);
+
+/* As aapdhg_set_scaling, each problem scaled on its own rows and columns.    */
+aapdhg_status aapdhg_batch_set_scaling(aapdhg_batch_t h, int32_t ruiz_iters, int32_t pock_chambolle);
+
+/* Starts of all problems (concatenated caller-order x0: sum(n[p]), y0:
+ * sum(m[p]); NULL = zeros), projected as in aapdhg_set_start; resets.        */
+aapdhg_status aapdhg_batch_set_start(aapdhg_batch_t h, const double *x0, const double *y0);
+aapdhg_status aapdhg_batch_reset(aapdhg_batch_t h);
+
+/* Run up to max_iters batch iterations (the first call also forms u^1 = T u^0
+ * of every problem first, as aapdhg_iterate does).  A problem's KKT residual
+ * is tested every kkt_every iterations (0: never); a problem stops when it is
+ * <= tol and is left unchanged from then on; the call returns early when every
+ * problem has stopped.  iters_done (optional): batch iterations run by this
+ * call.  A new call re-tests every converged problem against its tolerance.
+ * Returns AAPDHG_OK when every problem met the tolerance, AAPDHG_NOT_CONVERGED
+ * when max_iters ran out first, AAPDHG_ERR_NUMERIC (not sticky) when some
+ * problem stopped on NaN/Inf, or an error.                                   */
+aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double tol,
+                                   int32_t kkt_every, int64_t *iters_done);
+
+/* Current iterates of all problems in the caller's order, concatenated as the
+ * inputs (x: sum(n[p]), y: sum(m[p]); either may be NULL).                   */
+aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y);
+
+/* KKT quantities of every problem's current iterate: out6[6p .. 6p+5] as in
+ * aapdhg_get_kkt (host array of 6 * nprob).                                  */
+aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6);
+
+/* Per-problem status, out6[6p .. 6p+5] = {iterations, AA steps, PDHG steps,
+ * factorisation failures, converged (0/1), NaN/Inf met (0/1)}.               */
+aapdhg_status aapdhg_batch_get_status(aapdhg_batch_t h, int64_t *out6);
+
+/* CUDA-event timing of the batch kernels by kind: 0 half-step x, 1 half-step
+ * y, 2 memory pass, 3 AA mix, 4 per-problem KKT; kind -1 gives in *launches
+ * the number of kernels launched since profiling was last (re)set.          */
+aapdhg_status aapdhg_batch_profile_kernels(aapdhg_batch_t h, int32_t enable);
+aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, int64_t *launches,
+                                              double *total_ms);
+
+aapdhg_status aapdhg_batch_device_bytes(aapdhg_batch_t h, int64_t *bytes);
+const char *aapdhg_batch_last_error(aapdhg_batch_t h);
+void aapdhg_batch_destroy(aapdhg_batch_t h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -238,6 +238,39 @@ def large(seed=SEED_BASE + 3, m=2_000_000, n=5_000_000, z=50_000_000, exponent=2
     return construct(rng, m, n, rp, ci, v, sense, l, u, name=f"large-{m}x{n}")
 
 
+def batch_member(seed, m, n_per_m=2.5, nnz_mean=8.0, len_sigma=0.8) -> Problem:
+    """One LP of the batched workload: m rows, round(n_per_m * m) columns, row
+    lengths lognormal with mean nnz_mean (clipped to [1, min(2000, n)]) at
+    uniform columns, N(0,1) values times a per-row lognormal(0, 2) scale, 30%
+    '>=' rows, [0, U(1, 100)] bounds with 10% free variables; feasible with a
+    known optimum by construction."""
+    rng = np.random.default_rng(seed)
+    n = int(round(n_per_m * m))
+    mu = np.log(nnz_mean) - 0.5 * len_sigma ** 2
+    lens = np.clip(np.rint(rng.lognormal(mu, len_sigma, m)).astype(np.int64), 1, min(2000, n))
+    rows = np.repeat(np.arange(m, dtype=np.int64), lens)
+    cols = rng.integers(0, n, len(rows))
+    vals = rng.standard_normal(len(rows)) * np.exp(rng.normal(0.0, 2.0, m))[rows]
+    rp, ci, v = _csr_from_coo(m, rows, cols, vals)
+    sense = (rng.random(m) < 0.30).astype(np.int8)
+    l, u = _bounds_medium(rng, n)
+    return construct(rng, m, n, rp, ci, v, sense, l, u, name=f"batch-{m}x{n}")
+
+
+def batch_sizes(seed=SEED_BASE + 4, count=256, rows_min=1_000, rows_max=50_000):
+    """Row counts of the batched workload: log-uniform in [rows_min, rows_max]."""
+    rng = np.random.default_rng(seed)
+    return np.rint(np.exp(rng.uniform(np.log(rows_min), np.log(rows_max), count))).astype(np.int64)
+
+
+def batch(seed=SEED_BASE + 4, count=256, rows_min=1_000, rows_max=50_000, scale=1.0):
+    """The batched workload: `count` independent LPs of uneven size (rows
+    log-uniform in [rows_min, rows_max], scaled by `scale`), member p drawn by
+    batch_member with its own seed."""
+    ms = batch_sizes(seed, count, rows_min, rows_max)
+    return [batch_member(seed * 1000 + p, max(4, int(round(scale * int(mr))))) for p, mr in enumerate(ms)]
+
+
 def toy_feasibility() -> Problem:
     """min 0 s.t. x = 3, x >= 0 (Sec. 5.2, eq. simple-feasibility); optimum
     (x, y) = (3, 0)."""

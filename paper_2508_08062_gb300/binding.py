@@ -32,7 +32,15 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_iterate",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
            "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
-           "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy")
+           "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
+           "aapdhg_batch_create", "aapdhg_batch_set_steps", "aapdhg_batch_estimate_norms",
+           "aapdhg_batch_set_method", "aapdhg_batch_set_scaling", "aapdhg_batch_set_start",
+           "aapdhg_batch_reset", "aapdhg_batch_iterate", "aapdhg_batch_get_iterate",
+           "aapdhg_batch_get_kkt", "aapdhg_batch_get_status", "aapdhg_batch_profile_kernels",
+           "aapdhg_batch_get_kernel_profile", "aapdhg_batch_device_bytes",
+           "aapdhg_batch_last_error", "aapdhg_batch_destroy")
+NO_STATUS = ("aapdhg_last_error", "aapdhg_destroy", "aapdhg_batch_last_error",
+             "aapdhg_batch_destroy")
 
 
 class AAPDHGError(RuntimeError):
@@ -79,8 +87,27 @@ def load(path: str = LIB_PATH):
     L.aapdhg_last_error.restype = C.c_char_p
     L.aapdhg_destroy.argtypes = [vp]
     L.aapdhg_destroy.restype = None
+    L.aapdhg_batch_create.argtypes = [i32] + [vp] * 11 + [i32, vp, C.POINTER(vp)]
+    L.aapdhg_batch_set_steps.argtypes = [vp, vp, vp]
+    L.aapdhg_batch_estimate_norms.argtypes = [vp, i32, C.c_uint64, vp]
+    L.aapdhg_batch_set_method.argtypes = [vp, i32, i32, f64, f64, f64, f64, f64, f64, f64, i32,
+                                          i32]
+    L.aapdhg_batch_set_scaling.argtypes = [vp, i32, i32]
+    L.aapdhg_batch_set_start.argtypes = [vp, vp, vp]
+    L.aapdhg_batch_reset.argtypes = [vp]
+    L.aapdhg_batch_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
+    L.aapdhg_batch_get_iterate.argtypes = [vp, vp, vp]
+    L.aapdhg_batch_get_kkt.argtypes = [vp, vp]
+    L.aapdhg_batch_get_status.argtypes = [vp, vp]
+    L.aapdhg_batch_profile_kernels.argtypes = [vp, i32]
+    L.aapdhg_batch_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
+    L.aapdhg_batch_device_bytes.argtypes = [vp, C.POINTER(i64)]
+    L.aapdhg_batch_last_error.argtypes = [vp]
+    L.aapdhg_batch_last_error.restype = C.c_char_p
+    L.aapdhg_batch_destroy.argtypes = [vp]
+    L.aapdhg_batch_destroy.restype = None
     for name in EXPORTS:
-        if name not in ("aapdhg_last_error", "aapdhg_destroy"):
+        if name not in NO_STATUS:
             getattr(L, name).restype = st
     _lib = L
     return L
@@ -278,4 +305,150 @@ class Solver:
     def device_bytes(self):
         b = C.c_int64()
         self._check(self._L.aapdhg_device_bytes(self._h, C.byref(b)))
+        return b.value
+
+
+class BatchSolver:
+    """Many independent LPs advanced together on the GPU (the batched C ABI).
+
+    ``problems``: a sequence of objects like the ``Solver`` input.  Per-problem
+    quantities go in and come out as arrays over the problems (step sizes,
+    norms, KKT rows, status rows) or as lists of per-problem (x, y).
+    """
+
+    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "kkt")
+
+    def __init__(self, problems, precision: str = "mixed", stream=None, torch_memory: bool = True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the solver has no CPU path")
+        L = load()
+        if torch_memory:
+            use_torch_allocator()
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self._L = L
+        self._h = C.c_void_p()
+        self.nprob = len(problems)
+        self.m = np.array([int(P.m) for P in problems], dtype=np.int32)
+        self.n = np.array([int(P.n) for P in problems], dtype=np.int32)
+        nnz = np.array([int(np.asarray(P.row_ptr)[-1]) for P in problems], dtype=np.int64)
+        cat = lambda key, dt: np.ascontiguousarray(  # noqa: E731
+            np.concatenate([np.asarray(getattr(P, key), dtype=dt) for P in problems]), dtype=dt)
+        keep = (self.m, self.n, nnz, cat("row_ptr", np.int64), cat("col_idx", np.int32),
+                cat("val", np.float64), cat("sense", np.int8), cat("q", np.float64),
+                cat("c", np.float64), cat("l", np.float64), cat("u", np.float64))
+        s = L.aapdhg_batch_create(self.nprob, *[_ptr(a) for a in keep], PRECISIONS[precision],
+                                  C.c_void_p(stream.cuda_stream), C.byref(self._h))
+        if s != OK:
+            raise AAPDHGError(s, L.aapdhg_batch_last_error(None).decode())
+        self.xoff = np.concatenate([[0], np.cumsum(self.n.astype(np.int64))])
+        self.yoff = np.concatenate([[0], np.cumsum(self.m.astype(np.int64))])
+        self.precision = precision
+
+    def _check(self, s, allow=(OK,)):
+        if s not in allow:
+            raise AAPDHGError(s, self._L.aapdhg_batch_last_error(self._h).decode())
+        return s
+
+    def close(self):
+        if self._h:
+            self._L.aapdhg_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_steps(self, tau, sigma):
+        t = _f64(np.broadcast_to(np.asarray(tau, np.float64), (self.nprob,)), self.nprob)
+        g = _f64(np.broadcast_to(np.asarray(sigma, np.float64), (self.nprob,)), self.nprob)
+        self._check(self._L.aapdhg_batch_set_steps(self._h, _ptr(t), _ptr(g)))
+
+    def estimate_norms(self, iters=100, seed=1):
+        out = np.empty(self.nprob)
+        self._check(self._L.aapdhg_batch_estimate_norms(self._h, int(iters), int(seed), _ptr(out)))
+        return out
+
+    def set_method(self, method="aa", mem=5, D=10.0, eps=1.0, eta=1e-10, beta=1.0, c_s=0.2,
+                   kappa=1e8, c_div=1.0, dhat_mode=1, faa_adaptive=1):
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        self._check(self._L.aapdhg_batch_set_method(self._h, m, int(mem), D, eps, eta, beta, c_s,
+                                                    kappa, c_div, int(dhat_mode),
+                                                    int(faa_adaptive)))
+
+    def set_scaling(self, ruiz_iters=10, pock_chambolle=True):
+        self._check(self._L.aapdhg_batch_set_scaling(self._h, int(ruiz_iters),
+                                                     int(bool(pock_chambolle))))
+
+    def set_start(self, x0=None, y0=None):
+        """x0, y0: concatenated caller-order arrays, or lists of per-problem arrays."""
+        if isinstance(x0, (list, tuple)):
+            x0 = np.concatenate(x0)
+        if isinstance(y0, (list, tuple)):
+            y0 = np.concatenate(y0) if len(y0) else np.zeros(0)
+        x0 = None if x0 is None else _f64(x0, int(self.xoff[-1]))
+        y0 = None if y0 is None else _f64(y0, int(self.yoff[-1]))
+        self._check(self._L.aapdhg_batch_set_start(self._h, _ptr(x0), _ptr(y0)))
+
+    def reset(self):
+        self._check(self._L.aapdhg_batch_reset(self._h))
+
+    def iterate(self, max_iters, tol=0.0, kkt_every=0):
+        """Returns (all converged, batch iterations run)."""
+        done = C.c_int64()
+        s = self._check(self._L.aapdhg_batch_iterate(self._h, int(max_iters), float(tol),
+                                                     int(kkt_every), C.byref(done)),
+                        allow=(OK, NOT_CONVERGED, ERR_NUMERIC))
+        return s == OK, done.value
+
+    def get_iterate(self):
+        x = np.empty(int(self.xoff[-1]))
+        y = np.empty(int(self.yoff[-1]))
+        self._check(self._L.aapdhg_batch_get_iterate(self._h, _ptr(x), _ptr(y)))
+        return [(x[self.xoff[p]:self.xoff[p + 1]], y[self.yoff[p]:self.yoff[p + 1]])
+                for p in range(self.nprob)]
+
+    def get_kkt(self):
+        """(nprob, 6) array: r_p, r_d, r_g, KKT, c'x, dual objective."""
+        out = np.empty((self.nprob, 6))
+        self._check(self._L.aapdhg_batch_get_kkt(self._h, _ptr(out)))
+        return out
+
+    def status(self):
+        """(nprob, 6) int64: iterations, AA steps, PDHG steps, factorisation
+        failures, converged, NaN/Inf met."""
+        out = np.empty((self.nprob, 6), dtype=np.int64)
+        self._check(self._L.aapdhg_batch_get_status(self._h, _ptr(out)))
+        return out
+
+    def profile_kernels(self, enable=True):
+        self._check(self._L.aapdhg_batch_profile_kernels(self._h, int(bool(enable))))
+
+    def kernel_profile(self):
+        out = {}
+        for k, name in enumerate(self.KERNEL_KINDS):
+            n, ms = C.c_int64(), C.c_double()
+            self._check(self._L.aapdhg_batch_get_kernel_profile(self._h, k, C.byref(n),
+                                                                C.byref(ms)))
+            out[name] = dict(launches=n.value, total_ms=ms.value,
+                             avg_ms=(ms.value / n.value) if n.value else None)
+        return out
+
+    def launch_count(self):
+        n, ms = C.c_int64(), C.c_double()
+        self._check(self._L.aapdhg_batch_get_kernel_profile(self._h, -1, C.byref(n), C.byref(ms)))
+        return n.value
+
+    def device_bytes(self):
+        b = C.c_int64()
+        self._check(self._L.aapdhg_batch_device_bytes(self._h, C.byref(b)))
         return b.value

@@ -15,7 +15,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 def _sources():
     out = []
     for f in sorted(os.listdir(SRC_DIR)):
-        if f.endswith((".cu", ".cuh")):
+        if f.endswith((".cu", ".cuh", ".h")):
             out.append(os.path.join(SRC_DIR, f))
     out.append(os.path.join(ROOT, "include", "aapdhg.h"))
     return out
@@ -28,15 +28,30 @@ def stale() -> bool:
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
+UNITS = ("aapdhg.cu", "batch.cu", "kkt_noalloc.cu")
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile each translation unit in parallel (one nvcc per unit), then link."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [NVCC, "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", "-shared",
-           "-o", tmp, os.path.join(SRC_DIR, "aapdhg.cu"), os.path.join(SRC_DIR, "kkt_noalloc.cu")]
+    obj_dir = os.path.join(HERE, "_build")
+    os.makedirs(obj_dir, exist_ok=True)
+    flags = ["-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC"]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
+        flags.insert(0, "-Xptxas=-v")
+    procs, objs = [], []
+    for u in UNITS:
+        obj = os.path.join(obj_dir, u.replace(".cu", f".{os.getpid()}.o"))
+        objs.append(obj)
+        procs.append((u, subprocess.Popen([NVCC, *flags, "-c", "-o", obj, os.path.join(SRC_DIR, u)])))
+    failed = [u for u, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError(f"nvcc failed on {failed}")
+    tmp = LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call([NVCC, *ARCH, "-shared", "-o", tmp, *objs])
+    for o in objs:
+        os.remove(o)
     os.replace(tmp, LIB)
     return LIB
 

@@ -19,6 +19,7 @@
 #include "../../include/aapdhg.h"
 #include "anderson.cuh"
 #include "common.cuh"
+#include "host.h"
 #include "precond.cuh"
 #include "spmv.cuh"
 
@@ -33,63 +34,160 @@ thread_local std::string g_create_err;
 
 constexpr int CHUNK_ITERS = 64;   // iterations launched between two host polls
 
-struct HostCSR {
-    int32_t rows = 0;
-    std::vector<int32_t> rp, ci;
-    std::vector<double> val;
-};
+}  // namespace
 
-// Per-matrix device-side tables built on the host: chunk tables of the long
-// rows and the SELL-32 slices of the short rows (rows sorted longest first).
-struct LayoutHost {
-    int32_t n_long = 0, n_chunks = 0, n_slices = 0;
-    std::vector<int32_t> chunk_row, row_chunk0;
-    std::vector<int32_t> slice_ptr, slice_w, sell_ci;
-    std::vector<double> sell_val;
-};
+namespace aaph {
 
-LayoutHost build_layout(const HostCSR &A) {
-    LayoutHost L;
-    const int32_t R = A.rows;
+void *raw_alloc(size_t bytes) {
+    void *p = nullptr;
+    if (g_alloc) return g_alloc(bytes, g_ctx);
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void raw_free(void *p) {
+    if (g_free) g_free(p, g_ctx);
+    else cudaFree(p);
+}
+
+bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L) {
     auto len = [&](int32_t r) { return A.rp[r + 1] - A.rp[r]; };
-    int32_t nlong = 0;
-    while (nlong < R && len(nlong) > SELL_MAX) ++nlong;
-    L.row_chunk0.assign(nlong + 1, 0);
-    for (int32_t r = 0; r < nlong; ++r) {
-        const int32_t nch = (len(r) + LONG_CHUNK - 1) / LONG_CHUNK;
-        L.row_chunk0[r + 1] = L.row_chunk0[r] + nch;
-        for (int32_t c = 0; c < nch; ++c) L.chunk_row.push_back(r);
+    struct Slice { int32_t row0, rows, pid, width; };
+    std::vector<int32_t> long_rows, long_pid;
+    std::vector<Slice> sl;
+    for (const RowSeg &sg : segs) {
+        int32_t r = sg.row0;
+        const int32_t end = sg.row0 + sg.rows;
+        for (; r < end && len(r) > SELL_MAX; ++r) {
+            long_rows.push_back(r);
+            long_pid.push_back(sg.pid);
+        }
+        for (; r < end; r += 32) sl.push_back({r, std::min(32, end - r), sg.pid, len(r)});
     }
-    L.n_long = nlong;
-    L.n_chunks = L.row_chunk0[nlong];
-    const int32_t nshort = R - nlong;
-    L.n_slices = (nshort + 31) / 32;
-    L.slice_ptr.resize(L.n_slices + 1, 0);
-    L.slice_w.resize(L.n_slices, 0);
-    for (int32_t s = 0; s < L.n_slices; ++s) {
-        const int32_t r0 = nlong + 32 * s;
-        L.slice_w[s] = len(r0);                 // longest row of the slice comes first
-        L.slice_ptr[s + 1] = L.slice_ptr[s] + 32 * L.slice_w[s];
+    L.n_long = (int32_t)long_rows.size();
+    L.row_chunk0.assign(L.n_long + 1, 0);
+    for (int32_t lr = 0; lr < L.n_long; ++lr) {
+        const int32_t nch = (len(long_rows[lr]) + LONG_CHUNK - 1) / LONG_CHUNK;
+        L.row_chunk0[lr + 1] = L.row_chunk0[lr] + nch;
+        for (int32_t c = 0; c < nch; ++c) L.chunk_meta.push_back(make_int4(long_rows[lr], lr, long_pid[lr], 0));
     }
-    const int64_t total = L.slice_ptr[L.n_slices];
+    L.n_chunks = L.row_chunk0[L.n_long];
+    std::stable_sort(sl.begin(), sl.end(), [](const Slice &a, const Slice &b) { return a.width > b.width; });
+    L.n_slices = (int32_t)sl.size();
+    int64_t total = 0;
+    for (const Slice &x : sl) total += 32 * (int64_t)x.width;
+    if (total >= ((int64_t)1 << 31)) return false;
+    L.slice_meta.resize(L.n_slices);
     L.sell_ci.assign(total, 0);
     L.sell_val.assign(total, 0.0);
-    for (int32_t s = 0; s < L.n_slices; ++s) {
-        for (int32_t lane = 0; lane < 32; ++lane) {
-            const int32_t r = nlong + 32 * s + lane;
-            if (r >= R) break;
-            const int32_t lr = len(r);
-            for (int32_t t = 0; t < lr; ++t) {
-                const int64_t q = (int64_t)L.slice_ptr[s] + (int64_t)t * 32 + lane;
-                L.sell_ci[q] = A.ci[A.rp[r] + t];
-                L.sell_val[q] = A.val[A.rp[r] + t];
+    int32_t off = 0;
+    for (int32_t q = 0; q < L.n_slices; ++q) {
+        const Slice &x = sl[q];
+        L.slice_meta[q] = make_int4(off, x.width, x.row0, x.rows | (x.pid << 6));
+        for (int32_t lane = 0; lane < x.rows; ++lane) {
+            const int32_t r = x.row0 + lane, lrn = len(r);
+            for (int32_t t = 0; t < lrn; ++t) {
+                const int64_t k = (int64_t)off + (int64_t)t * 32 + lane;
+                L.sell_ci[k] = A.ci[A.rp[r] + t];
+                L.sell_val[k] = A.val[A.rp[r] + t];
+            }
+        }
+        off += 32 * x.width;
+    }
+    return true;
+}
+
+void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                    std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
+                    HostCSR &KT) {
+    std::vector<int64_t> rlen(m), clen(n, 0);
+    for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
+    for (int64_t k = 0; k < rp[m]; ++k) clen[ci[k]]++;
+    perm_y.resize(m);
+    perm_x.resize(n);
+    for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
+    for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
+    std::stable_sort(perm_y.begin(), perm_y.end(), [&](int32_t a, int32_t b) { return rlen[a] > rlen[b]; });
+    std::stable_sort(perm_x.begin(), perm_x.end(), [&](int32_t a, int32_t b) { return clen[a] > clen[b]; });
+    std::vector<int32_t> inv_x(n), inv_y(m);
+    for (int32_t j = 0; j < n; ++j) inv_x[perm_x[j]] = j;
+    for (int32_t i = 0; i < m; ++i) inv_y[perm_y[i]] = i;
+    const int64_t Z = rp[m];
+    // K' rows (internal x) with internal y column indices: counting sort over
+    // internal x while walking internal rows in order -> ascending columns.
+    KT.rows = n;
+    KT.rp.assign(n + 1, 0);
+    for (int32_t j = 0; j < n; ++j) KT.rp[j + 1] = KT.rp[j] + (int32_t)clen[perm_x[j]];
+    KT.ci.resize(Z);
+    KT.val.resize(Z);
+    {
+        std::vector<int32_t> pos(KT.rp.begin(), KT.rp.end() - 1);
+        for (int32_t ii = 0; ii < m; ++ii) {
+            const int32_t i = perm_y[ii];
+            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+                const int32_t jj = inv_x[ci[k]];
+                const int32_t p = pos[jj]++;
+                KT.ci[p] = ii;
+                KT.val[p] = val[k];
             }
         }
     }
-    return L;
+    // K rows (internal y) with internal x columns, ascending: transpose K'.
+    K.rows = m;
+    K.rp.assign(m + 1, 0);
+    for (int32_t ii = 0; ii < m; ++ii) K.rp[ii + 1] = K.rp[ii] + (int32_t)rlen[perm_y[ii]];
+    K.ci.resize(Z);
+    K.val.resize(Z);
+    {
+        std::vector<int32_t> pos(K.rp.begin(), K.rp.end() - 1);
+        for (int32_t jj = 0; jj < n; ++jj)
+            for (int32_t p = KT.rp[jj]; p < KT.rp[jj + 1]; ++p) {
+                const int32_t ii = KT.ci[p];
+                const int32_t q = pos[ii]++;
+                K.ci[q] = jj;
+                K.val[q] = KT.val[p];
+            }
+    }
 }
 
-}  // namespace
+std::string validate_lp(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
+                        const int32_t *col_idx, const double *val, const int8_t *row_sense,
+                        const double *q, const double *c, const double *lb, const double *ub) {
+    if (m < 0 || n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31)) return "need m >= 0, n >= 1, 0 <= nnz < 2^31";
+    if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || (m > 0 && (!row_sense || !q)) || !c || !lb || !ub)
+        return "NULL input array";
+    if (row_ptr[0] != 0 || row_ptr[m] != nnz) return "row_ptr[0] must be 0 and row_ptr[m] must be nnz";
+    std::vector<int32_t> mark(n, -1);
+    for (int32_t i = 0; i < m; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr is not non-decreasing";
+        if (row_sense[i] != AAPDHG_ROW_EQ && row_sense[i] != AAPDHG_ROW_GE)
+            return "row_sense must be 0 (=) or 1 (>=)";
+        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+            const int32_t j = col_idx[k];
+            if (j < 0 || j >= n) return "column index out of range";
+            if (mark[j] == i) return "repeated column within a row";
+            mark[j] = i;
+        }
+    }
+    for (int64_t k = 0; k < nnz; ++k)
+        if (!std::isfinite(val[k])) return "non-finite value in K, q or c";
+    for (int32_t i = 0; i < m; ++i)
+        if (!std::isfinite(q[i])) return "non-finite value in K, q or c";
+    for (int32_t j = 0; j < n; ++j)
+        if (!std::isfinite(c[j])) return "non-finite value in K, q or c";
+    for (int32_t j = 0; j < n; ++j) {
+        if (std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] > ub[j] || lb[j] == INFINITY || ub[j] == -INFINITY)
+            return "bounds must satisfy lb <= ub, lb < +inf, ub > -inf";
+    }
+    return "";
+}
+
+}  // namespace aaph
+
+using namespace aaph;
 
 struct DevAlloc {
     void *p;
@@ -176,13 +274,7 @@ aapdhg_status fail(aapdhg_t h, aapdhg_status s, const std::string &msg) {
 void *dev_alloc(aapdhg_t h, size_t bytes) {
     if (bytes == 0) bytes = 16;
     bytes = (bytes + 255) & ~(size_t)255;
-    void *p = nullptr;
-    if (g_alloc) {
-        p = g_alloc(bytes, g_ctx);
-    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
-        cudaGetLastError();
-        p = nullptr;
-    }
+    void *p = raw_alloc(bytes);
     if (p) {
         h->allocs.push_back({p, bytes});
         h->bytes += (int64_t)bytes;
@@ -191,10 +283,7 @@ void *dev_alloc(aapdhg_t h, size_t bytes) {
 }
 
 void dev_free_all(aapdhg_t h) {
-    for (auto &a : h->allocs) {
-        if (g_free) g_free(a.p, g_ctx);
-        else cudaFree(a.p);
-    }
+    for (auto &a : h->allocs) raw_free(a.p);
     h->allocs.clear();
     h->bytes = 0;
 }
@@ -208,82 +297,6 @@ T *alloc_copy(aapdhg_t h, const T *src, size_t count, bool *ok) {
         *ok = false;
     }
     return d;
-}
-
-// Build the internal CSR of K (rows renumbered longest-first, columns mapped
-// to the internal variable order) and of K' (likewise), both with column
-// indices ascending within each row.
-void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, const double *val,
-                    std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
-                    HostCSR &KT) {
-    std::vector<int64_t> rlen(m), clen(n, 0);
-    for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
-    for (int64_t k = 0; k < rp[m]; ++k) clen[ci[k]]++;
-    perm_y.resize(m);
-    perm_x.resize(n);
-    for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
-    for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
-    std::stable_sort(perm_y.begin(), perm_y.end(), [&](int32_t a, int32_t b) { return rlen[a] > rlen[b]; });
-    std::stable_sort(perm_x.begin(), perm_x.end(), [&](int32_t a, int32_t b) { return clen[a] > clen[b]; });
-    std::vector<int32_t> inv_x(n), inv_y(m);
-    for (int32_t j = 0; j < n; ++j) inv_x[perm_x[j]] = j;
-    for (int32_t i = 0; i < m; ++i) inv_y[perm_y[i]] = i;
-    const int64_t Z = rp[m];
-    // K' rows (internal x) with internal y column indices: counting sort over
-    // internal x while walking internal rows in order -> ascending columns.
-    KT.rows = n;
-    KT.rp.assign(n + 1, 0);
-    for (int32_t j = 0; j < n; ++j) KT.rp[j + 1] = KT.rp[j] + (int32_t)clen[perm_x[j]];
-    KT.ci.resize(Z);
-    KT.val.resize(Z);
-    {
-        std::vector<int32_t> pos(KT.rp.begin(), KT.rp.end() - 1);
-        for (int32_t ii = 0; ii < m; ++ii) {
-            const int32_t i = perm_y[ii];
-            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-                const int32_t jj = inv_x[ci[k]];
-                const int32_t p = pos[jj]++;
-                KT.ci[p] = ii;
-                KT.val[p] = val[k];
-            }
-        }
-    }
-    // K rows (internal y) with internal x columns, ascending: transpose K'.
-    K.rows = m;
-    K.rp.assign(m + 1, 0);
-    for (int32_t ii = 0; ii < m; ++ii) K.rp[ii + 1] = K.rp[ii] + (int32_t)rlen[perm_y[ii]];
-    K.ci.resize(Z);
-    K.val.resize(Z);
-    {
-        std::vector<int32_t> pos(K.rp.begin(), K.rp.end() - 1);
-        for (int32_t jj = 0; jj < n; ++jj)
-            for (int32_t p = KT.rp[jj]; p < KT.rp[jj + 1]; ++p) {
-                const int32_t ii = KT.ci[p];
-                const int32_t q = pos[ii]++;
-                K.ci[q] = jj;
-                K.val[q] = KT.val[p];
-            }
-    }
-}
-
-// D-hat of the Remark on its construction (mode 1) or the identity (mode 0):
-// per row of K' (a variable) and per row of K (a constraint),
-// sqrt(max(max |entry|, 1e-10)).  One warp per row, lanes striding its entries.
-template <typename V>
-__global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mode, V *dh) {
-    const int64_t N = (int64_t)n + m;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < N; e += warps) {
-        if (mode == 0) { if (lane == 0) dh[e] = V(1); continue; }
-        const CSRView<V> &A = e < n ? KT : K;
-        const int32_t r = (int32_t)(e < n ? e : e - n);
-        double mx = 0.0;
-        for (int32_t k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) mx = fmax(mx, fabs((double)A.val[k]));
-#pragma unroll
-        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane == 0) dh[e] = (V)sqrt(fmax(mx, 1e-10));
-    }
 }
 
 // ||v||_2^2 of a vector into st->scratch[slot] (last-block finalize).
@@ -358,40 +371,10 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     P.N = N;
     P.Npad = h->Npad;
 
-    auto to_v = [](const std::vector<double> &a) {
-        std::vector<V> o(a.size());
-        for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
-        return o;
-    };
     auto mk_csr = [&](const HostCSR &A, CSRView<V> &view) {
-        LayoutHost L = build_layout(A);
-        view.rows = A.rows;
-        view.rp = alloc_copy(h, A.rp.data(), A.rp.size(), &ok);
-        view.ci = alloc_copy(h, A.ci.data(), std::max<size_t>(A.ci.size(), 1), &ok);
-        std::vector<V> v = to_v(A.val);
-        if (v.empty()) v.push_back(V(0));
-        view.val = alloc_copy(h, v.data(), v.size(), &ok);
-        view.n_long = L.n_long;
-        view.n_chunks = L.n_chunks;
-        view.n_slices = L.n_slices;
-        auto nonempty = [](std::vector<int32_t> x) { if (x.empty()) x.push_back(0); return x; };
-        std::vector<int32_t> cr = nonempty(L.chunk_row), sci = nonempty(L.sell_ci);
-        std::vector<int2> meta(std::max(1, L.n_slices));
-        for (int32_t q = 0; q < L.n_slices; ++q) meta[q] = make_int2(L.slice_ptr[q], L.slice_w[q]);
-        view.chunk_row = alloc_copy(h, cr.data(), cr.size(), &ok);
-        view.row_chunk0 = alloc_copy(h, L.row_chunk0.data(), L.row_chunk0.size(), &ok);
-        view.slice_meta = alloc_copy(h, meta.data(), meta.size(), &ok);
-        view.sell_ci = alloc_copy(h, sci.data(), sci.size(), &ok);
-        std::vector<V> sv = to_v(L.sell_val);
-        if (sv.empty()) sv.push_back(V(0));
-        view.sell_val = alloc_copy(h, sv.data(), sv.size(), &ok);
-        view.chunk_part = (V *)dev_alloc(h, sizeof(V) * 2 * std::max(1, L.n_chunks));
-        view.chunk_cnt = (uint32_t *)dev_alloc(h, sizeof(uint32_t) * std::max(1, L.n_long));
-        if (!view.chunk_part || !view.chunk_cnt) ok = false;
-        else if (cudaMemsetAsync(view.chunk_cnt, 0, sizeof(uint32_t) * std::max(1, L.n_long),
-                                 h->stream) != cudaSuccess) ok = false;
-        // the host vectors above are pageable: make the copies complete before they go
-        if (cudaStreamSynchronize(h->stream) != cudaSuccess) ok = false;
+        LayoutHost L;
+        if (!build_layout(A, {RowSeg{0, A.rows, 0}}, L)) { ok = false; return; }
+        if (!upload_csr<V>(A, L, view, [&](size_t b) { return dev_alloc(h, b); }, h->stream)) ok = false;
     };
     mk_csr(KT, P.KT);
     mk_csr(K, P.K);
@@ -423,8 +406,10 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
 
     // fixed grids (deterministic reductions)
     int occ1 = 0, occ2 = 0, occ3 = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep<V, true>, BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep<V, true>, BLOCK, 0);
+    // grids sized for the common (non-KKT) variants, all of whose blocks are
+    // resident; a KKT launch (one in kkt_every) may run a short second wave
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep<V, false>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep<V, false>, BLOCK, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, 20>, BLOCK, 0);
     const int64_t tasksT = P.KT.ntasks(), tasksK = P.K.ntasks();
     P.grid1 = grid_for(h, (tasksT + WARPS - 1) / WARPS, occ1);
@@ -785,11 +770,6 @@ template <typename V> aapdhg_status set_scaling_t(aapdhg_t h, int32_t ruiz_iters
     return AAPDHG_OK;
 }
 
-bool finite_all(const double *a, int64_t n) {
-    for (int64_t i = 0; i < n; ++i)
-        if (!std::isfinite(a[i])) return false;
-    return true;
-}
 
 }  // namespace
 
@@ -847,30 +827,9 @@ aapdhg_status aapdhg_create(int32_t m, int32_t n, int64_t nnz, const int64_t *ro
         row_sense = se_h.data(); c = c_h.data(); lb = lb_h.data(); ub = ub_h.data();
     }
 
-    // ---- validation --------------------------------------------------------
-    if (row_ptr[0] != 0 || row_ptr[m] != nnz)
-        return fail(nullptr, AAPDHG_ERR_INVALID, "row_ptr[0] must be 0 and row_ptr[m] must be nnz");
     {
-        std::vector<int32_t> mark(n, -1);
-        for (int32_t i = 0; i < m; ++i) {
-            if (row_ptr[i + 1] < row_ptr[i])
-                return fail(nullptr, AAPDHG_ERR_INVALID, "row_ptr is not non-decreasing");
-            if (row_sense[i] != AAPDHG_ROW_EQ && row_sense[i] != AAPDHG_ROW_GE)
-                return fail(nullptr, AAPDHG_ERR_INVALID, "row_sense must be 0 (=) or 1 (>=)");
-            for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const int32_t j = col_idx[k];
-                if (j < 0 || j >= n) return fail(nullptr, AAPDHG_ERR_INVALID, "column index out of range");
-                if (mark[j] == i) return fail(nullptr, AAPDHG_ERR_INVALID, "repeated column within a row");
-                mark[j] = i;
-            }
-        }
-    }
-    if (!finite_all(val, nnz) || !finite_all(q, m) || !finite_all(c, n))
-        return fail(nullptr, AAPDHG_ERR_INVALID, "non-finite value in K, q or c");
-    for (int32_t j = 0; j < n; ++j) {
-        if (std::isnan(lb[j]) || std::isnan(ub[j]) || lb[j] > ub[j] || lb[j] == INFINITY ||
-            ub[j] == -INFINITY)
-            return fail(nullptr, AAPDHG_ERR_INVALID, "bounds must satisfy lb <= ub, lb < +inf, ub > -inf");
+        const std::string why = validate_lp(m, n, nnz, row_ptr, col_idx, val, row_sense, q, c, lb, ub);
+        if (!why.empty()) return fail(nullptr, AAPDHG_ERR_INVALID, why);
     }
 
     aapdhg_t h = new (std::nothrow) aapdhg_s();

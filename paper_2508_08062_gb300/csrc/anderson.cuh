@@ -31,7 +31,7 @@ namespace aap {
 
 // Cholesky A = L L' in place (lower triangle).  Returns false when a pivot is
 // not positive (or not finite).
-__device__ bool warp_cholesky(double *A, int k) {
+static __device__ bool warp_cholesky(double *A, int k) {
     const int lane = threadIdx.x & 31;
     bool ok = true;
     for (int j = 0; j < k; ++j) {
@@ -55,7 +55,7 @@ __device__ bool warp_cholesky(double *A, int k) {
 }
 
 // Solve L L' x = b (b overwritten by x), lane 0.
-__device__ void chol_solve_lane0(const double *L, double *b, int k) {
+static __device__ void chol_solve_lane0(const double *L, double *b, int k) {
     if ((threadIdx.x & 31) != 0) return;
     for (int i = 0; i < k; ++i) {
         double s = b[i];
@@ -85,7 +85,7 @@ struct SolveSmem {
 
 // FAA selection (Alg. 4-6) from the Gram matrix.  Input: list (oldest first,
 // k columns).  Output: sm.kept[0..nk) oldest first.  One warp.
-__device__ void faa_select(const DevState *st, int k, double c_s, double kappa, SolveSmem &sm) {
+static __device__ void faa_select(const DevState *st, int k, double c_s, double kappa, SolveSmem &sm) {
     const int lane = threadIdx.x & 31;
     // Reverse (Alg. 6): newest first
     for (int t = lane; t < k; t += 32) sm.ord[t] = st->list[k - 1 - t];
@@ -171,7 +171,7 @@ __device__ void faa_select(const DevState *st, int k, double c_s, double kappa, 
 
 // Solve for gamma over columns cols[0..k) (oldest first): Cholesky of the
 // Gram block + eta I.  Writes st->use / st->gamma.  One warp.  Returns ok.
-__device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, SolveSmem &sm) {
+static __device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, SolveSmem &sm) {
     const int lane = threadIdx.x & 31;
     for (int idx = lane; idx < k * k; idx += 32) {
         const int a = idx / k, b = idx % k;
@@ -196,6 +196,81 @@ __device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, Sol
     return ok;
 }
 
+// The m x m work of one iteration for one LP, run by warp 0 of one block after
+// the memory pass's partial sums are reduced into red[]: the Gram row and
+// column of the new slot, the incremental right-hand side, the column list,
+// and, when the safeguard passed (st->want_aa), the solve of Alg. 2 or the
+// filters and solve of Alg. 3; then the counters and the next free slot.
+template <int MC>
+__device__ void memory_finalize(DevState *st, const MethodParams &mp, int M, const int *s_old,
+                                int nold, int sn, const double *red, SolveSmem &sm, const Trace &tr) {
+    const int lane = threadIdx.x & 31;
+    int accept = 0, lsfail = 0;
+    if (M > 0) {
+        // Gram row / column of the new slot; incremental right-hand side
+        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
+        for (int t = lane; t < nold; t += 32) {
+            const int s = s_old[t];
+            st->G[s * NSLOT + sn] = red[t];
+            st->G[sn * NSLOT + s] = red[t];
+            st->rhs[s] += red[t];
+            st->list[t] = s;
+        }
+        if (lane == 0) {
+            st->G[sn * NSLOT + sn] = red[MC];
+            st->rhs[sn] = red[MC + 1];
+            st->en2[sn] = red[MC + 2];
+            st->list[nold] = sn;
+            st->count = nold + 1;
+            st->new_slot = sn;
+        }
+        __syncwarp();
+        if (st->want_aa) {
+            const int k = st->count;
+            if (mp.method == 1) {
+                sm.nk = k;
+                for (int t = lane; t < k; t += 32) sm.kept[t] = st->list[t];
+                __syncwarp();
+                const bool ok = gram_solve(st, sm.kept, k, mp.eta, sm);
+                accept = ok ? 1 : 0;
+                lsfail = ok ? 0 : 1;
+            } else {
+                faa_select(st, k, mp.c_s, mp.kappa, sm);
+                const int nk = sm.nk;
+                bool ok = true;
+                if (nk > 0) ok = gram_solve(st, sm.kept, nk, 0.0, sm);
+                else if (lane == 0) st->use_count = 0;
+                __syncwarp();
+                accept = ok ? 1 : 0;
+                lsfail = ok ? 0 : 1;
+                if (ok && mp.faa_adaptive) {
+                    for (int t = lane; t < nk; t += 32) st->list[t] = sm.kept[t];
+                    if (lane == 0) st->count = nk;
+                }
+            }
+        }
+        __syncwarp();
+        // slot for the next column's du: the lowest slot not in the list
+        const int cnt = st->count;
+        unsigned long long used = 0ull;
+        for (int t = lane; t < cnt; t += 32) used |= 1ull << st->list[t];
+#pragma unroll
+        for (int o = 16; o; o >>= 1) used |= __shfl_xor_sync(0xffffffffu, used, o);
+        if (lane == 0) st->free_slot = __ffsll((long long)~used) - 1;
+    }
+    if (lane == 0) {
+        const int64_t it = st->it;
+        st->accept = accept;
+        if (accept) st->n_aa += 1; else st->n_pd += 1;
+        if (lsfail) st->n_lsfail += 1;
+        if (it < tr.cap) {
+            tr.branch[it] = (int8_t)(accept ? 1 : (lsfail ? 2 : 0));
+            tr.mk[it] = accept ? st->use_count : -1;
+        }
+        st->it = it + 1;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Per-element work of the memory pass on W consecutive elements at e0.  The
 // old columns are read in groups of 8 with all loads of a group issued before
@@ -203,10 +278,12 @@ __device__ bool gram_solve(DevState *st, const int *cols, int k, double eta, Sol
 // ---------------------------------------------------------------------------
 constexpr int COLGRP = 8;
 
-template <typename V, int MC, int W>
+// GN: also accumulate ||g^k||^2 into acc[MC + 3] (the batched path forms the
+// safeguard's residual norm here rather than in the half-steps).
+template <typename V, int MC, int W, bool GN = false>
 __device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int cur, bool prev_acc,
                                              V beta, V *DGn, V *Wn, const int64_t *off, int nold,
-                                             Acc<V> (&acc)[MC + 3]) {
+                                             Acc<V> (&acc)[MC + 3 + (GN ? 1 : 0)]) {
     const V *UPs = reinterpret_cast<const V *>(P.UP);
     const Pack<V, W> pa = ld<V, W>(UPs + 2 * e0), pb = ld<V, W>(UPs + 2 * e0 + W);
     const Pack<V, W> gp = ld<V, W>(P.g + e0);
@@ -230,6 +307,7 @@ __device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int c
         acc[MC].add_sq(dg[i]);
         acc[MC + 1].add_prod(dg[i], g);
         acc[MC + 2].add_sq(du);
+        if constexpr (GN) acc[MC + 3].add_sq(g);
     }
     st<V, W>(P.g + e0, gk);
     st<V, W>(DGn + e0, dgk);
@@ -352,71 +430,7 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
-    int accept = 0, lsfail = 0;
-    if (M > 0) {
-        // Gram row / column of the new slot; incremental right-hand side
-        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
-        for (int t = lane; t < nold; t += 32) {
-            const int s = s_old[t];
-            st->G[s * NSLOT + sn] = red[t];
-            st->G[sn * NSLOT + s] = red[t];
-            st->rhs[s] += red[t];
-            st->list[t] = s;
-        }
-        if (lane == 0) {
-            st->G[sn * NSLOT + sn] = red[MC];
-            st->rhs[sn] = red[MC + 1];
-            st->en2[sn] = red[MC + 2];
-            st->list[nold] = sn;
-            st->count = nold + 1;
-            st->new_slot = sn;
-        }
-        __syncwarp();
-        if (st->want_aa) {
-            const int k = st->count;
-            if (mp.method == 1) {
-                sm.nk = k;
-                for (int t = lane; t < k; t += 32) sm.kept[t] = st->list[t];
-                __syncwarp();
-                const bool ok = gram_solve(st, sm.kept, k, mp.eta, sm);
-                accept = ok ? 1 : 0;
-                lsfail = ok ? 0 : 1;
-            } else {
-                faa_select(st, k, mp.c_s, mp.kappa, sm);
-                const int nk = sm.nk;
-                bool ok = true;
-                if (nk > 0) ok = gram_solve(st, sm.kept, nk, 0.0, sm);
-                else if (lane == 0) st->use_count = 0;
-                __syncwarp();
-                accept = ok ? 1 : 0;
-                lsfail = ok ? 0 : 1;
-                if (ok && mp.faa_adaptive) {
-                    for (int t = lane; t < nk; t += 32) st->list[t] = sm.kept[t];
-                    if (lane == 0) st->count = nk;
-                }
-            }
-        }
-        __syncwarp();
-        // slot for the next column's du: the lowest slot not in the list
-        const int cnt = st->count;
-        unsigned long long used = 0ull;
-        for (int t = lane; t < cnt; t += 32) used |= 1ull << st->list[t];
-#pragma unroll
-        for (int o = 16; o; o >>= 1) used |= __shfl_xor_sync(0xffffffffu, used, o);
-        if (lane == 0) st->free_slot = __ffsll((long long)~used) - 1;
-    }
-    if (lane == 0) {
-        const int64_t it = st->it;
-        st->accept = accept;
-        if (accept) st->n_aa += 1; else st->n_pd += 1;
-        if (lsfail) st->n_lsfail += 1;
-        if (it < P.tr.cap) {
-            P.tr.branch[it] = (int8_t)(accept ? 1 : (lsfail ? 2 : 0));
-            P.tr.mk[it] = accept ? st->use_count : -1;
-        }
-        st->it = it + 1;
-    }
+    memory_finalize<MC>(st, mp, M, s_old, nold, sn, red, sm, P.tr);
 }
 
 // ---------------------------------------------------------------------------

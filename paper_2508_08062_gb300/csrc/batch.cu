@@ -1,0 +1,935 @@
+// Host runtime and C ABI of the batched solver (aapdhg_batch_*): many
+// independent LPs packed into one block-diagonal LP and advanced together by
+// the kernels of batch.cuh.
+//
+// create():  validate every LP, renumber each one's rows and columns
+//            longest-first (as the single-LP solver does), pad its variable
+//            and constraint ranges to multiples of 4, pack K and K' of all
+//            problems into one matrix each (SELL slices of all problems
+//            ordered by width), cut each problem's elements into chunks for
+//            the per-problem reductions, and move everything to the device.
+// iterate(): the kernel sequence of one batch iteration, in CUDA graphs of
+//            CHUNK_ITERS iterations; once per chunk the host reads the
+//            per-problem state headers (one strided copy) and stops when every
+//            problem has met the tolerance or failed.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/aapdhg.h"
+#include "batch.cuh"
+#include "host.h"
+#include "precond.cuh"
+
+using namespace aap;
+using namespace aaph;
+
+namespace {
+
+constexpr int B_CHUNK_ITERS = 64;
+thread_local std::string g_batch_create_err;
+
+// Per-problem header read by the host each chunk: it, n_aa, n_pd, n_lsfail,
+// done, error, init_done (the leading fields of DevState), 8-byte aligned.
+constexpr size_t HDR = (offsetof(DevState, want_aa) + 7) & ~(size_t)7;
+
+enum { BK_XSTEP = 0, BK_YSTEP = 1, BK_MEMORY = 2, BK_MIX = 3, BK_KKT = 4, BK_N = 5 };
+
+}  // namespace
+
+struct aapdhg_batch_s {
+    int32_t nprob = 0;
+    int32_t prec = AAPDHG_MIXED;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0, sm_count = 0;
+    aapdhg_status sticky = AAPDHG_OK;
+    std::string err;
+    struct Alloc { void *p; size_t bytes; };
+    std::vector<Alloc> allocs;
+    int64_t bytes = 0;
+
+    // problem p: caller sizes, padded sizes, offsets of its variables and
+    // constraints in the packed order, and its renumbering (internal -> caller)
+    std::vector<int32_t> m, n, nxp, nyp;
+    std::vector<int64_t> xoff, yoff, xcat, ycat;   // packed offsets; offsets into caller arrays
+    std::vector<int32_t> perm_x, perm_y;           // concatenated, local indices
+    std::vector<double> lo_x, hi_x, x0, y0;        // caller order, concatenated
+    std::vector<int8_t> sense;
+    std::vector<double> tau, sigma;
+    int64_t n_tot = 0, m_tot = 0, N = 0, Npad = 0;
+
+    Prob<float> pf{};
+    Prob<double> pd{};
+    BatchView<float> bf{};
+    BatchView<double> bd{};
+    MethodParams mp{};
+    DevState *stb = nullptr;
+    unsigned char *hdr_host = nullptr;             // pinned: nprob headers
+    int64_t g = 0;                                 // batch iterations launched (the start one included)
+    int32_t kkt_every = 0;
+    int32_t dhat_mode = -1;
+    bool scaled = false;
+    std::vector<double> dr, dc;                    // Dr (m_tot), Dc (n_tot) in packed order
+    bool have_rings = false;
+    // CUDA graphs of full chunks keyed by (KKT phase, parity, kkt_every, tol)
+    cudaStream_t cap_stream = nullptr;
+    struct GraphEntry { cudaGraphExec_t exec; int64_t phase; int parity; int32_t kkt_every; double tol; };
+    std::vector<GraphEntry> graphs;
+    bool use_graphs = true;
+    // instrumentation
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_kind;
+    double prof_ms[BK_N] = {0, 0, 0, 0, 0};
+    int64_t prof_n[BK_N] = {0, 0, 0, 0, 0};
+    int64_t launches = 0;
+};
+
+typedef aapdhg_batch_s *bh_t;
+
+namespace {
+
+aapdhg_status bfail(bh_t h, aapdhg_status s, const std::string &msg) {
+    if (h) {
+        if (h->sticky == AAPDHG_OK) {
+            h->sticky = s;
+            h->err = msg;
+        }
+    } else {
+        g_batch_create_err = msg;
+    }
+    return s;
+}
+
+#define BCK(h, call)                                                                          \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return bfail((h), AAPDHG_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+void *bdev_alloc(bh_t h, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = raw_alloc(bytes);
+    if (p) {
+        h->allocs.push_back({p, bytes});
+        h->bytes += (int64_t)bytes;
+    }
+    return p;
+}
+
+template <typename T> T *bput(bh_t h, const std::vector<T> &src, bool *ok) {
+    T *d = (T *)bdev_alloc(h, sizeof(T) * std::max<size_t>(src.size(), 1));
+    if (!d) { *ok = false; return nullptr; }
+    if (!src.empty() &&
+        cudaMemcpyAsync(d, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        *ok = false;
+    return d;
+}
+
+template <typename V> Prob<V> &bprob(bh_t h);
+template <> Prob<float> &bprob<float>(bh_t h) { return h->pf; }
+template <> Prob<double> &bprob<double>(bh_t h) { return h->pd; }
+template <typename V> BatchView<V> &bview(bh_t h);
+template <> BatchView<float> &bview<float>(bh_t h) { return h->bf; }
+template <> BatchView<double> &bview<double>(bh_t h) { return h->bd; }
+
+int bgrid(bh_t h, int64_t need, int occ) {
+    const int64_t cap = (int64_t)h->sm_count * std::max(occ, 1);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
+}
+
+void bmark_begin(bh_t h, int kind) {
+    h->launches += 1;
+    if (!h->prof_on) return;
+    const size_t need = 2 * (h->ev_kind.size() + 1);
+    while (h->ev.size() < need) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { h->prof_on = false; return; }
+        h->ev.push_back(e);
+    }
+    cudaEventRecord(h->ev[2 * h->ev_kind.size()], h->stream);
+    h->ev_kind.push_back(kind);
+}
+
+void bmark_end(bh_t h) {
+    if (!h->prof_on || h->ev_kind.empty()) return;
+    cudaEventRecord(h->ev[2 * h->ev_kind.size() - 1], h->stream);
+}
+
+void bcollect(bh_t h) {
+    for (size_t i = 0; i < h->ev_kind.size(); ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->ev[2 * i], h->ev[2 * i + 1]) == cudaSuccess) {
+            h->prof_ms[h->ev_kind[i]] += ms;
+            h->prof_n[h->ev_kind[i]] += 1;
+        }
+    }
+    h->ev_kind.clear();
+}
+
+void bdrop_graphs(bh_t h) {
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
+// ---------------------------------------------------------------------------
+// set-up
+// ---------------------------------------------------------------------------
+template <typename V>
+aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vector<RowSeg> &segK,
+                     const std::vector<RowSeg> &segKT, const std::vector<double> &cv,
+                     const std::vector<double> &qv, const std::vector<double> &lov,
+                     const std::vector<double> &hiv, const std::vector<double> &pnorm) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    bool ok = true;
+    P.m = (int32_t)h->m_tot;
+    P.n = (int32_t)h->n_tot;
+    P.N = h->N;
+    P.Npad = h->Npad;
+    auto alloc = [&](size_t b) { return bdev_alloc(h, b); };
+    for (int which = 0; which < 2 && ok; ++which) {
+        LayoutHost L;
+        const HostCSR &A = which ? K : KT;
+        if (!build_layout(A, which ? segK : segKT, L))
+            return bfail(h, AAPDHG_ERR_INVALID, "packed SELL storage exceeds 2^31 entries");
+        if (!upload_csr<V>(A, L, which ? P.K : P.KT, alloc, h->stream)) ok = false;
+    }
+    auto to_v = [](const std::vector<double> &a) {
+        std::vector<V> o(a.size());
+        for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
+        return o;
+    };
+    P.c = bput(h, to_v(cv), &ok);
+    P.q = bput(h, to_v(qv), &ok);
+    P.lo = bput(h, to_v(lov), &ok);
+    P.hi = bput(h, to_v(hiv), &ok);
+    P.UP = (V2 *)bdev_alloc(h, sizeof(V2) * h->N);
+    P.dh = (V *)bdev_alloc(h, sizeof(V) * h->N);
+    P.g = (V *)bdev_alloc(h, sizeof(V) * h->N);
+    P.DG = P.W = nullptr;
+    P.sc_x = P.sc_y = nullptr;
+    P.part1 = P.part2 = P.part3 = nullptr;
+    P.tr = Trace{0, nullptr, nullptr, nullptr, nullptr};
+    P.st = nullptr;
+    if (!P.UP || !P.dh || !P.g) ok = false;
+    int occ1 = 0, occ2 = 0;
+    // grids for the common (non-KKT) variants: all their blocks resident
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep_b<V, false>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep_b<V, false>, BLOCK, 0);
+    P.grid1 = bgrid(h, (P.KT.ntasks() + WARPS - 1) / WARPS, occ1);
+    P.grid2 = bgrid(h, (P.K.ntasks() + WARPS - 1) / WARPS, occ2);
+
+    // chunks of every problem's elements: its variables, then its constraints
+    std::vector<int4> chunk;
+    std::vector<int32_t> pchunk0(h->nprob + 1, 0);
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        pchunk0[p] = (int32_t)chunk.size();
+        for (int part = 0; part < 2; ++part) {
+            const int64_t base = part ? h->n_tot + h->yoff[p] : h->xoff[p];
+            const int64_t len = part ? h->nyp[p] : h->nxp[p];
+            for (int64_t e = 0; e < len; e += BCHUNK)
+                chunk.push_back(make_int4(p, (int32_t)(base + e), (int32_t)std::min<int64_t>(BCHUNK, len - e), part));
+        }
+    }
+    pchunk0[h->nprob] = (int32_t)chunk.size();
+    B.nprob = h->nprob;
+    B.n_tot = h->n_tot;
+    B.m_tot = h->m_tot;
+    B.nchunk = (int32_t)chunk.size();
+    B.chunk = bput(h, chunk, &ok);
+    B.pchunk0 = bput(h, pchunk0, &ok);
+    B.pnorm = bput(h, pnorm, &ok);
+    B.tau = (const double *)bdev_alloc(h, sizeof(double) * h->nprob);
+    B.sigma = (const double *)bdev_alloc(h, sizeof(double) * h->nprob);
+    B.stb = (DevState *)bdev_alloc(h, sizeof(DevState) * h->nprob);
+    B.kterm = (V *)bdev_alloc(h, sizeof(V) * (3 * h->n_tot + 2 * h->m_tot));
+    B.cpart = (double *)bdev_alloc(h, sizeof(double) * NBV * B.nchunk);
+    B.pcnt = (uint32_t *)bdev_alloc(h, sizeof(uint32_t) * h->nprob);
+    if (!B.tau || !B.sigma || !B.stb || !B.kterm || !B.cpart || !B.pcnt) ok = false;
+    if (!ok) return bfail(h, AAPDHG_ERR_OOM, "device allocation or copy failed during create");
+    h->stb = B.stb;
+    BCK(h, cudaMemsetAsync(B.stb, 0, sizeof(DevState) * h->nprob, h->stream));
+    BCK(h, cudaMemsetAsync(B.pcnt, 0, sizeof(uint32_t) * h->nprob, h->stream));
+    BCK(h, cudaMemsetAsync(B.kterm, 0, sizeof(V) * (3 * h->n_tot + 2 * h->m_tot), h->stream));
+    k_dhat<V><<<bgrid(h, (h->N + WARPS - 1) / WARPS, 8), BLOCK, 0, h->stream>>>(
+        P.KT, P.K, P.n, P.m, 1, const_cast<V *>(P.dh));
+    BCK(h, cudaGetLastError());
+    h->dhat_mode = 1;
+    BCK(h, cudaStreamSynchronize(h->stream));
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status bensure_rings(bh_t h) {
+    Prob<V> &P = bprob<V>(h);
+    if (h->have_rings) return AAPDHG_OK;
+    P.DG = (V *)bdev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
+    P.W = (V *)bdev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
+    if (!P.DG || !P.W) return bfail(h, AAPDHG_ERR_OOM, "device allocation of the Anderson memory failed");
+    h->have_rings = true;
+    return AAPDHG_OK;
+}
+
+// Start of every problem: u^0 (projected start, scaled when the LP is) in
+// component 0, state cleared, batch counter at 0.
+template <typename V> aapdhg_status breset(bh_t h) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = bprob<V>(h);
+    std::vector<V2> up(h->N);
+    for (auto &e : up) { e.x = V(0); e.y = V(0); }
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        const int32_t *px = h->perm_x.data() + h->xcat[p];
+        const int32_t *py = h->perm_y.data() + h->ycat[p];
+        for (int32_t j = 0; j < h->n[p]; ++j) {
+            const int64_t e = h->xoff[p] + j;
+            const double v = h->x0[h->xcat[p] + px[j]];
+            up[e].x = (V)(h->scaled ? v / h->dc[e] : v);
+        }
+        for (int32_t i = 0; i < h->m[p]; ++i) {
+            const int64_t r = h->yoff[p] + i;
+            const double v = h->y0[h->ycat[p] + py[i]];
+            up[h->n_tot + r].x = (V)(h->scaled ? v / h->dr[r] : v);
+        }
+    }
+    BCK(h, cudaMemcpyAsync(P.UP, up.data(), sizeof(V2) * h->N, cudaMemcpyHostToDevice, h->stream));
+    BCK(h, cudaMemsetAsync(h->stb, 0, sizeof(DevState) * h->nprob, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    h->g = 0;
+    return AAPDHG_OK;
+}
+
+aapdhg_status breset_any(bh_t h) { return h->prec == AAPDHG_FP64 ? breset<double>(h) : breset<float>(h); }
+
+// ---------------------------------------------------------------------------
+// one batch iteration
+// ---------------------------------------------------------------------------
+template <typename V, int MC> void blaunch_memory_mix(bh_t h, int cur) {
+    Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
+    bmark_begin(h, BK_MEMORY);
+    k_memory_b<V, MC><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
+    bmark_end(h);
+    if (M > 0) {
+        bmark_begin(h, BK_MIX);
+        k_mix_b<V, MC><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
+        bmark_end(h);
+    }
+}
+
+template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
+    Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    const int cur = (int)(g & 1);
+    const bool kkt = mode == MODE_EVAL || (h->kkt_every > 0 && g >= 1 && (g - 1) % h->kkt_every == 0);
+    bmark_begin(h, BK_XSTEP);
+    if (kkt) k_xstep_b<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else k_xstep_b<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    bmark_end(h);
+    bmark_begin(h, BK_YSTEP);
+    if (kkt) k_ystep_b<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else k_ystep_b<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    bmark_end(h);
+    if (kkt) {
+        bmark_begin(h, BK_KKT);
+        k_kkt_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(B, h->mp.tol, mode);
+        bmark_end(h);
+    }
+    if (mode == MODE_EVAL) return;
+    const int M = h->mp.mem;
+    if (M <= 4) blaunch_memory_mix<V, 4>(h, cur);
+    else if (M <= 8) blaunch_memory_mix<V, 8>(h, cur);
+    else if (M <= 16) blaunch_memory_mix<V, 16>(h, cur);
+    else blaunch_memory_mix<V, 32>(h, cur);
+}
+
+int launches_per_iter(bh_t h, int64_t g) {
+    const bool kkt = h->kkt_every > 0 && g >= 1 && (g - 1) % h->kkt_every == 0;
+    const bool mix = h->mp.method != 0 && h->mp.mem > 0;
+    return 3 + (kkt ? 1 : 0) + (mix ? 1 : 0);
+}
+
+template <typename V> bool blaunch_chunk_graph(bh_t h, int64_t g0) {
+    if (!h->use_graphs || h->prof_on) return false;
+    const int64_t phase = h->kkt_every > 0 ? (g0 - 1) % h->kkt_every : 0;
+    const int parity = (int)(g0 & 1);
+    const double tol = h->mp.tol;
+    int64_t nl = 0;
+    for (int64_t c = 0; c < B_CHUNK_ITERS; ++c) nl += launches_per_iter(h, g0 + c);
+    for (auto &e : h->graphs)
+        if (e.phase == phase && e.parity == parity && e.kkt_every == h->kkt_every && e.tol == tol) {
+            if (cudaGraphLaunch(e.exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+            h->launches += nl;
+            return true;
+        }
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        h->use_graphs = false;
+        return false;
+    }
+    if (h->graphs.size() >= 8) bdrop_graphs(h);
+    cudaStream_t user = h->stream;
+    h->stream = h->cap_stream;
+    cudaGraph_t graph = nullptr;
+    bool ok = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    const int64_t saved = h->launches;
+    if (ok) {
+        for (int64_t c = 0; c < B_CHUNK_ITERS; ++c) blaunch_iteration<V>(h, g0 + c, MODE_ITER);
+        ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess;
+    }
+    h->stream = user;
+    h->launches = saved;
+    cudaGraphExec_t exec = nullptr;
+    if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+    if (graph) cudaGraphDestroy(graph);
+    if (!ok) {
+        cudaGetLastError();
+        h->use_graphs = false;
+        return false;
+    }
+    h->graphs.push_back({exec, phase, parity, h->kkt_every, tol});
+    if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
+    h->launches += nl;
+    return true;
+}
+
+// Per-problem headers into hdr_host (one strided copy) after a stream sync.
+aapdhg_status bread_headers(bh_t h) {
+    BCK(h, cudaMemcpy2DAsync(h->hdr_host, HDR, h->stb, sizeof(DevState), HDR, h->nprob,
+                             cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    bcollect(h);
+    return AAPDHG_OK;
+}
+
+const DevState *hdr(bh_t h, int32_t p) { return reinterpret_cast<const DevState *>(h->hdr_host + HDR * p); }
+
+template <typename V> aapdhg_status biterate(bh_t h, int64_t max_iters, double tol, int32_t kkt_every,
+                                            int64_t *iters_done) {
+    h->mp.tol = tol;
+    h->kkt_every = kkt_every;
+    aapdhg_status s = AAPDHG_OK;
+    if (h->mp.method != 0 && h->mp.mem > 0 && (s = bensure_rings<V>(h)) != AAPDHG_OK) return s;
+    if (h->g == 0) {
+        blaunch_iteration<V>(h, 0, MODE_ITER);   // u^1 = T u^0 and g^0 of every problem
+        h->g = 1;
+    } else {
+        k_batch_clear_done<<<(h->nprob + 255) / 256, 256, 0, h->stream>>>(h->stb, h->nprob);
+        h->launches += 1;
+    }
+    BCK(h, cudaGetLastError());
+    if ((s = bread_headers(h)) != AAPDHG_OK) return s;
+    auto all_stopped = [&]() {
+        for (int32_t p = 0; p < h->nprob; ++p)
+            if (!hdr(h, p)->done && !hdr(h, p)->error) return false;
+        return true;
+    };
+    int64_t launched = 0;
+    bool stop = all_stopped();
+    while (launched < max_iters && !stop) {
+        const int64_t chunk = std::min<int64_t>(B_CHUNK_ITERS, max_iters - launched);
+        if (!(chunk == B_CHUNK_ITERS && blaunch_chunk_graph<V>(h, h->g)))
+            for (int64_t c = 0; c < chunk; ++c) blaunch_iteration<V>(h, h->g + c, MODE_ITER);
+        BCK(h, cudaGetLastError());
+        h->g += chunk;
+        launched += chunk;
+        if ((s = bread_headers(h)) != AAPDHG_OK) return s;
+        stop = all_stopped();
+    }
+    if (iters_done) *iters_done = launched;
+    bool any_err = false, all_done = true;
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        any_err |= hdr(h, p)->error != 0;
+        all_done &= hdr(h, p)->done != 0;
+    }
+    if (any_err) {
+        h->err = "NaN or Inf in the iterate of at least one problem (see aapdhg_batch_get_status)";
+        return AAPDHG_ERR_NUMERIC;
+    }
+    return all_done ? AAPDHG_OK : AAPDHG_NOT_CONVERGED;
+}
+
+template <typename V> aapdhg_status bget_iterate(bh_t h, double *x, double *y) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = bprob<V>(h);
+    const int cur = (int)(h->g & 1);
+    std::vector<V2> up(h->N);
+    BCK(h, cudaMemcpyAsync(up.data(), P.UP, sizeof(V2) * h->N, cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        const int32_t *px = h->perm_x.data() + h->xcat[p];
+        const int32_t *py = h->perm_y.data() + h->ycat[p];
+        if (x)
+            for (int32_t j = 0; j < h->n[p]; ++j) {
+                const int64_t e = h->xoff[p] + j;
+                const double v = (double)(cur ? up[e].y : up[e].x);
+                x[h->xcat[p] + px[j]] = h->scaled ? v * h->dc[e] : v;
+            }
+        if (y)
+            for (int32_t i = 0; i < h->m[p]; ++i) {
+                const int64_t r = h->yoff[p] + i;
+                const double v = (double)(cur ? up[h->n_tot + r].y : up[h->n_tot + r].x);
+                y[h->ycat[p] + py[i]] = h->scaled ? v * h->dr[r] : v;
+            }
+    }
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status bget_kkt(bh_t h, double *out) {
+    blaunch_iteration<V>(h, h->g, MODE_EVAL);
+    BCK(h, cudaGetLastError());
+    BCK(h, cudaMemcpy2DAsync(out, 6 * sizeof(double), reinterpret_cast<const char *>(h->stb) + offsetof(DevState, kkt),
+                             sizeof(DevState), 6 * sizeof(double), h->nprob, cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    bcollect(h);
+    return AAPDHG_OK;
+}
+
+// Power iteration on every K_p' K_p at once (the Sec. 5.1 step-size rule): the
+// packed SpMVs, then per-problem norms and normalisation over each problem's
+// variable segment.  Each problem's start vector is the single-LP one for the
+// same seed (splitmix64 over its internal variable order).
+template <typename V> aapdhg_status bestimate_norms(bh_t h, int32_t iters, uint64_t seed, double *norms) {
+    Prob<V> &P = bprob<V>(h);
+    const size_t mark = h->allocs.size();
+    V *v = (V *)bdev_alloc(h, sizeof(V) * h->n_tot);
+    V *w = (V *)bdev_alloc(h, sizeof(V) * std::max<int64_t>(h->m_tot, 1));
+    double *part = (double *)bdev_alloc(h, sizeof(double) * std::max(P.grid1, P.grid2));
+    double *ss = (double *)bdev_alloc(h, sizeof(double) * h->nprob);
+    int64_t *off = (int64_t *)bdev_alloc(h, sizeof(int64_t) * (h->nprob + 1));
+    if (!v || !w || !part || !ss || !off) return bfail(h, AAPDHG_ERR_OOM, "power iteration buffers");
+    std::vector<V> hv(h->n_tot, V(0));
+    std::vector<int64_t> hoff(h->nprob + 1);
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        uint64_t z = seed ? seed : 0x9E3779B97F4A7C15ull;
+        for (int32_t j = 0; j < h->n[p]; ++j) {
+            z += 0x9E3779B97F4A7C15ull;
+            uint64_t t = z;
+            t = (t ^ (t >> 30)) * 0xBF58476D1CE4E5B9ull;
+            t = (t ^ (t >> 27)) * 0x94D049BB133111EBull;
+            t ^= t >> 31;
+            hv[h->xoff[p] + j] = (V)((double)(t >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0);
+        }
+        hoff[p] = h->xoff[p];
+    }
+    hoff[h->nprob] = h->n_tot;
+    BCK(h, cudaMemcpyAsync(v, hv.data(), sizeof(V) * h->n_tot, cudaMemcpyHostToDevice, h->stream));
+    BCK(h, cudaMemcpyAsync(off, hoff.data(), sizeof(int64_t) * (h->nprob + 1), cudaMemcpyHostToDevice, h->stream));
+    for (int32_t t = 0; t < iters; ++t) {
+        if (h->m_tot > 0) k_spmv_plain<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P.K, v, w, part);
+        k_spmv_plain<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P.KT, w, v, part);
+        k_seg_sumsq<V><<<h->nprob, BLOCK, 0, h->stream>>>(v, off, ss);
+        k_seg_scale<V><<<h->nprob, BLOCK, 0, h->stream>>>(v, off, ss);
+        BCK(h, cudaGetLastError());
+    }
+    std::vector<double> hs(h->nprob);
+    BCK(h, cudaMemcpyAsync(hs.data(), ss, sizeof(double) * h->nprob, cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    // ||K'K v|| of the last (unit) v is sqrt(ss); the norm of K is its square root
+    for (int32_t p = 0; p < h->nprob; ++p) norms[p] = sqrt(sqrt(hs[p]));
+    while (h->allocs.size() > mark) {
+        auto a = h->allocs.back();
+        h->allocs.pop_back();
+        h->bytes -= (int64_t)a.bytes;
+        raw_free(a.p);
+    }
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status bset_scaling(bh_t h, int32_t ruiz_iters, int32_t pc) {
+    Prob<V> &P = bprob<V>(h);
+    const int64_t m = h->m_tot, n = h->n_tot;
+    V *dr = (V *)bdev_alloc(h, sizeof(V) * std::max<int64_t>(m, 1));
+    V *dc = (V *)bdev_alloc(h, sizeof(V) * n);
+    V *tr = (V *)bdev_alloc(h, sizeof(V) * std::max<int64_t>(m, 1));
+    V *tc = (V *)bdev_alloc(h, sizeof(V) * n);
+    V *scx = (V *)bdev_alloc(h, sizeof(V) * n);
+    V *scy = (V *)bdev_alloc(h, sizeof(V) * std::max<int64_t>(m, 1));
+    if (!dr || !dc || !tr || !tc || !scx || !scy) return bfail(h, AAPDHG_ERR_OOM, "scaling buffers");
+    cudaStream_t s = h->stream;
+    const int gv = bgrid(h, (h->N + BLOCK - 1) / BLOCK, 4);
+    const int gr = bgrid(h, (h->N + WARPS - 1) / WARPS, 8);
+    k_fill<V><<<gv, BLOCK, 0, s>>>(dr, V(1), m);
+    k_fill<V><<<gv, BLOCK, 0, s>>>(dc, V(1), n);
+    for (int32_t pass = 0; pass < ruiz_iters + (pc ? 1 : 0); ++pass) {
+        const int sum = pass >= ruiz_iters;
+        if (m > 0) k_row_norm<V><<<gr, BLOCK, 0, s>>>(P.K, sum, tr);
+        k_row_norm<V><<<gr, BLOCK, 0, s>>>(P.KT, sum, tc);
+        k_factor<V><<<gv, BLOCK, 0, s>>>(tr, m);
+        k_factor<V><<<gv, BLOCK, 0, s>>>(tc, n);
+        if (m > 0) k_scale_matrix<V><<<gr, BLOCK, 0, s>>>(P.K, tr, tc);
+        k_scale_matrix<V><<<gr, BLOCK, 0, s>>>(P.KT, tc, tr);
+        k_vmul<V><<<gv, BLOCK, 0, s>>>(dr, tr, m);
+        k_vmul<V><<<gv, BLOCK, 0, s>>>(dc, tc, n);
+    }
+    k_vmul<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.c), dc, n);
+    k_vmul<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.q), dr, m);
+    k_vdiv<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.lo), dc, n);
+    k_vdiv<V><<<gv, BLOCK, 0, s>>>(const_cast<V *>(P.hi), dc, n);
+    k_vinv<V><<<gv, BLOCK, 0, s>>>(scx, dc, n);
+    k_vinv<V><<<gv, BLOCK, 0, s>>>(scy, dr, m);
+    BCK(h, cudaGetLastError());
+    std::vector<V> hr(std::max<int64_t>(m, 1)), hc(n);
+    BCK(h, cudaMemcpyAsync(hr.data(), dr, sizeof(V) * m, cudaMemcpyDeviceToHost, s));
+    BCK(h, cudaMemcpyAsync(hc.data(), dc, sizeof(V) * n, cudaMemcpyDeviceToHost, s));
+    BCK(h, cudaStreamSynchronize(s));
+    h->dr.assign(hr.begin(), hr.begin() + m);
+    h->dc.assign(hc.begin(), hc.end());
+    P.sc_x = scx;
+    P.sc_y = m > 0 ? scy : nullptr;
+    k_dhat<V><<<gr, BLOCK, 0, s>>>(P.KT, P.K, P.n, P.m, h->dhat_mode < 0 ? 1 : h->dhat_mode,
+                                   const_cast<V *>(P.dh));
+    BCK(h, cudaGetLastError());
+    h->scaled = true;
+    return AAPDHG_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+aapdhg_status aapdhg_batch_create(int32_t nprob, const int32_t *m, const int32_t *n, const int64_t *nnz,
+                                  const int64_t *row_ptr, const int32_t *col_idx, const double *val,
+                                  const int8_t *row_sense, const double *q, const double *c,
+                                  const double *lb, const double *ub, int32_t precision,
+                                  void *cuda_stream, aapdhg_batch_t *out) {
+    if (!out) return bfail(nullptr, AAPDHG_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (nprob < 1 || nprob >= (1 << 25) || !m || !n || !nnz || !row_ptr)
+        return bfail(nullptr, AAPDHG_ERR_INVALID, "need 1 <= nprob < 2^25 and non-NULL size arrays");
+    if (precision != AAPDHG_FP64 && precision != AAPDHG_MIXED)
+        return bfail(nullptr, AAPDHG_ERR_INVALID, "unknown precision");
+    // offsets of each problem in the concatenated caller arrays; validation
+    std::vector<int64_t> rpc(nprob), kc(nprob), xc(nprob), yc(nprob);
+    int64_t R = 0, Z = 0, X = 0, Y = 0, xt = 0, yt = 0;
+    for (int32_t p = 0; p < nprob; ++p) {
+        if (m[p] < 0 || n[p] < 1 || nnz[p] < 0)
+            return bfail(nullptr, AAPDHG_ERR_INVALID, "problem " + std::to_string(p) + ": need m >= 0, n >= 1, nnz >= 0");
+        rpc[p] = R; kc[p] = Z; xc[p] = X; yc[p] = Y;
+        R += m[p] + 1; Z += nnz[p]; X += n[p]; Y += m[p];
+        xt += (n[p] + 3) & ~3; yt += (m[p] + 3) & ~3;
+    }
+    if (Z >= ((int64_t)1 << 31) || xt + yt >= ((int64_t)1 << 31))
+        return bfail(nullptr, AAPDHG_ERR_INVALID, "the packed batch needs < 2^31 nonzeros and elements");
+    for (int32_t p = 0; p < nprob; ++p) {
+        const std::string why = validate_lp(
+            m[p], n[p], nnz[p], row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
+            nnz[p] ? val + kc[p] : nullptr, m[p] ? row_sense + yc[p] : nullptr, m[p] ? q + yc[p] : nullptr,
+            c ? c + xc[p] : nullptr, lb ? lb + xc[p] : nullptr, ub ? ub + xc[p] : nullptr);
+        if (!why.empty()) return bfail(nullptr, AAPDHG_ERR_INVALID, "problem " + std::to_string(p) + ": " + why);
+    }
+
+    bh_t h = new (std::nothrow) aapdhg_batch_s();
+    if (!h) return bfail(nullptr, AAPDHG_ERR_OOM, "host allocation");
+    h->nprob = nprob;
+    h->prec = precision;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) {
+        if (cuda_stream) h->stream = (cudaStream_t)cuda_stream;
+        else { e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking); h->own_stream = true; }
+    }
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&h->hdr_host, HDR * (size_t)nprob);
+    if (e != cudaSuccess) {
+        std::string msg = std::string("CUDA setup: ") + cudaGetErrorString(e);
+        if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+        delete h;
+        return bfail(nullptr, AAPDHG_ERR_CUDA, msg);
+    }
+    h->m.assign(m, m + nprob);
+    h->n.assign(n, n + nprob);
+    h->nxp.resize(nprob);
+    h->nyp.resize(nprob);
+    h->xoff.resize(nprob);
+    h->yoff.resize(nprob);
+    h->xcat = xc;
+    h->ycat = yc;
+    for (int32_t p = 0; p < nprob; ++p) {
+        h->nxp[p] = (n[p] + 3) & ~3;
+        h->nyp[p] = (m[p] + 3) & ~3;
+        h->xoff[p] = h->n_tot;
+        h->yoff[p] = h->m_tot;
+        h->n_tot += h->nxp[p];
+        h->m_tot += h->nyp[p];
+    }
+    h->N = h->n_tot + h->m_tot;
+    h->Npad = (h->N + 63) & ~(int64_t)63;
+    h->lo_x.assign(lb, lb + X);
+    h->hi_x.assign(ub, ub + X);
+    h->sense.assign(row_sense ? row_sense : (const int8_t *)nullptr, row_sense ? row_sense + Y : nullptr);
+    h->tau.assign(nprob, 0.0);
+    h->sigma.assign(nprob, 0.0);
+
+    // per-problem renumbering, packed into one K and one K'
+    HostCSR K, KT;
+    K.rows = (int32_t)h->m_tot;
+    KT.rows = (int32_t)h->n_tot;
+    K.rp.assign(h->m_tot + 1, 0);
+    KT.rp.assign(h->n_tot + 1, 0);
+    K.ci.reserve(Z); K.val.reserve(Z); KT.ci.reserve(Z); KT.val.reserve(Z);
+    std::vector<double> cv(h->n_tot, 0.0), qv(std::max<int64_t>(h->m_tot, 1), 0.0);
+    std::vector<double> lov(h->N, 0.0), hiv(h->N, 0.0), pnorm(2 * (size_t)nprob);
+    std::vector<RowSeg> segK, segKT;
+    h->perm_x.reserve(X);
+    h->perm_y.reserve(Y);
+    for (int32_t p = 0; p < nprob; ++p) {
+        std::vector<int32_t> px, py;
+        HostCSR Kp, KTp;
+        const int32_t mp_ = m[p], np_ = n[p];
+        build_internal(mp_, np_, row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
+                       nnz[p] ? val + kc[p] : nullptr, px, py, Kp, KTp);
+        const int64_t xo = h->xoff[p], yo = h->yoff[p];
+        for (int32_t ii = 0; ii < h->nyp[p]; ++ii) {
+            if (ii < mp_)
+                for (int32_t k = Kp.rp[ii]; k < Kp.rp[ii + 1]; ++k) {
+                    K.ci.push_back((int32_t)(xo + Kp.ci[k]));
+                    K.val.push_back(Kp.val[k]);
+                }
+            K.rp[yo + ii + 1] = (int32_t)K.ci.size();
+        }
+        for (int32_t jj = 0; jj < h->nxp[p]; ++jj) {
+            if (jj < np_)
+                for (int32_t k = KTp.rp[jj]; k < KTp.rp[jj + 1]; ++k) {
+                    KT.ci.push_back((int32_t)(yo + KTp.ci[k]));
+                    KT.val.push_back(KTp.val[k]);
+                }
+            KT.rp[xo + jj + 1] = (int32_t)KT.ci.size();
+        }
+        segK.push_back(RowSeg{(int32_t)yo, h->nyp[p], p});
+        segKT.push_back(RowSeg{(int32_t)xo, h->nxp[p], p});
+        double q2 = 0.0, c2 = 0.0;
+        for (int32_t j = 0; j < np_; ++j) {
+            const int64_t oj = xc[p] + px[j];
+            cv[xo + j] = c[oj];
+            lov[xo + j] = lb[oj];
+            hiv[xo + j] = ub[oj];
+            c2 += c[oj] * c[oj];
+        }
+        for (int32_t i = 0; i < h->nyp[p]; ++i) {
+            const int64_t e2 = h->n_tot + yo + i;
+            hiv[e2] = INFINITY;
+            lov[e2] = -INFINITY;
+            if (i < mp_) {
+                const int64_t oi = yc[p] + py[i];
+                qv[yo + i] = q[oi];
+                lov[e2] = row_sense[oi] == AAPDHG_ROW_GE ? 0.0 : -INFINITY;
+                q2 += q[oi] * q[oi];
+            }
+        }
+        pnorm[2 * p] = sqrt(q2);
+        pnorm[2 * p + 1] = sqrt(c2);
+        h->perm_x.insert(h->perm_x.end(), px.begin(), px.end());
+        h->perm_y.insert(h->perm_y.end(), py.begin(), py.end());
+    }
+    qv.resize(std::max<int64_t>(h->m_tot, 1));
+    aapdhg_status s = precision == AAPDHG_FP64
+                          ? bsetup<double>(h, K, KT, segK, segKT, cv, qv, lov, hiv, pnorm)
+                          : bsetup<float>(h, K, KT, segK, segKT, cv, qv, lov, hiv, pnorm);
+    if (s == AAPDHG_OK) {
+        h->mp.method = AAPDHG_AA; h->mp.mem = 5; h->mp.D = 10.0; h->mp.eps = 1.0;
+        h->mp.eta = 1e-10; h->mp.beta = 1.0; h->mp.c_s = 0.2; h->mp.kappa = 1e8; h->mp.c_div = 1.0;
+        h->mp.faa_adaptive = 1;
+        aapdhg_batch_set_start(h, nullptr, nullptr);
+        s = h->sticky;
+    }
+    if (s != AAPDHG_OK) {
+        g_batch_create_err = h->err;
+        aapdhg_batch_destroy(h);
+        return s;
+    }
+    *out = h;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_set_steps(aapdhg_batch_t h, const double *tau, const double *sigma) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!tau || !sigma) return bfail(h, AAPDHG_ERR_INVALID, "tau and sigma arrays are required");
+    for (int32_t p = 0; p < h->nprob; ++p)
+        if (!(tau[p] > 0) || !(sigma[p] > 0) || !std::isfinite(tau[p]) || !std::isfinite(sigma[p]))
+            return bfail(h, AAPDHG_ERR_INVALID, "tau and sigma must be finite and > 0");
+    h->tau.assign(tau, tau + h->nprob);
+    h->sigma.assign(sigma, sigma + h->nprob);
+    const double *dt = h->prec == AAPDHG_FP64 ? h->bd.tau : h->bf.tau;
+    const double *ds = h->prec == AAPDHG_FP64 ? h->bd.sigma : h->bf.sigma;
+    BCK(h, cudaMemcpyAsync(const_cast<double *>(dt), tau, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+    BCK(h, cudaMemcpyAsync(const_cast<double *>(ds), sigma, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+    bdrop_graphs(h);
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_estimate_norms(aapdhg_batch_t h, int32_t iters, uint64_t seed, double *norms) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!norms || iters < 1) return bfail(h, AAPDHG_ERR_INVALID, "bad arguments");
+    return h->prec == AAPDHG_FP64 ? bestimate_norms<double>(h, iters, seed, norms)
+                                  : bestimate_norms<float>(h, iters, seed, norms);
+}
+
+aapdhg_status aapdhg_batch_set_method(aapdhg_batch_t h, int32_t method, int32_t m_A, double D, double eps,
+                                      double eta, double beta, double c_s, double kappa, double c_div,
+                                      int32_t dhat_mode, int32_t faa_adaptive) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (method < 0 || method > 2 || m_A < 0 || m_A > AAPDHG_MAX_MEMORY || !(D > 0) || !(eps > 0) ||
+        !(eta >= 0) || !(beta > 0 && beta <= 1) || !(c_s > 0 && c_s <= 1) || !(kappa > 0) ||
+        !(c_div >= 1) || (dhat_mode != 0 && dhat_mode != 1))
+        return bfail(h, AAPDHG_ERR_INVALID, "method parameters out of range");
+    h->mp.method = method; h->mp.mem = m_A; h->mp.D = D; h->mp.eps = eps; h->mp.eta = eta;
+    h->mp.beta = beta; h->mp.c_s = c_s; h->mp.kappa = kappa; h->mp.c_div = c_div;
+    h->mp.faa_adaptive = faa_adaptive ? 1 : 0;
+    bdrop_graphs(h);
+    if (dhat_mode != h->dhat_mode) {
+        const int gD = bgrid(h, (h->N + WARPS - 1) / WARPS, 8);
+        if (h->prec == AAPDHG_FP64)
+            k_dhat<double><<<gD, BLOCK, 0, h->stream>>>(h->pd.KT, h->pd.K, h->pd.n, h->pd.m, dhat_mode,
+                                                        const_cast<double *>(h->pd.dh));
+        else
+            k_dhat<float><<<gD, BLOCK, 0, h->stream>>>(h->pf.KT, h->pf.K, h->pf.n, h->pf.m, dhat_mode,
+                                                       const_cast<float *>(h->pf.dh));
+        BCK(h, cudaGetLastError());
+        h->dhat_mode = dhat_mode;
+    }
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_set_scaling(aapdhg_batch_t h, int32_t ruiz_iters, int32_t pock_chambolle) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (h->scaled || ruiz_iters < 0 || ruiz_iters > 1000)
+        return bfail(h, AAPDHG_ERR_INVALID, "scaling is applied at most once, with 0..1000 Ruiz passes");
+    bdrop_graphs(h);
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? bset_scaling<double>(h, ruiz_iters, pock_chambolle)
+                                             : bset_scaling<float>(h, ruiz_iters, pock_chambolle);
+    if (s != AAPDHG_OK) return s;
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_set_start(aapdhg_batch_t h, const double *x0, const double *y0) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    const size_t X = h->lo_x.size(), Y = h->sense.size();
+    h->x0.assign(X, 0.0);
+    h->y0.assign(Y, 0.0);
+    for (size_t j = 0; j < X; ++j) {
+        const double v = x0 ? x0[j] : 0.0;
+        if (!std::isfinite(v)) return bfail(h, AAPDHG_ERR_INVALID, "non-finite start");
+        h->x0[j] = std::min(std::max(v, h->lo_x[j]), h->hi_x[j]);
+    }
+    for (size_t i = 0; i < Y; ++i) {
+        double v = y0 ? y0[i] : 0.0;
+        if (!std::isfinite(v)) return bfail(h, AAPDHG_ERR_INVALID, "non-finite start");
+        if (h->sense[i] == AAPDHG_ROW_GE && v < 0) v = 0;
+        h->y0[i] = v;
+    }
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_reset(aapdhg_batch_t h) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double tol, int32_t kkt_every,
+                                   int64_t *iters_done) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (max_iters < 0 || kkt_every < 0 || !(tol >= 0))
+        return bfail(h, AAPDHG_ERR_INVALID, "need max_iters >= 0, kkt_every >= 0, tol >= 0");
+    for (int32_t p = 0; p < h->nprob; ++p)
+        if (!(h->tau[p] > 0)) return bfail(h, AAPDHG_ERR_INVALID, "set_steps must be called before iterate");
+    return h->prec == AAPDHG_FP64 ? biterate<double>(h, max_iters, tol, kkt_every, iters_done)
+                                  : biterate<float>(h, max_iters, tol, kkt_every, iters_done);
+}
+
+aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return h->prec == AAPDHG_FP64 ? bget_iterate<double>(h, x, y) : bget_iterate<float>(h, x, y);
+}
+
+aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!out6) return bfail(h, AAPDHG_ERR_INVALID, "out6 is NULL");
+    return h->prec == AAPDHG_FP64 ? bget_kkt<double>(h, out6) : bget_kkt<float>(h, out6);
+}
+
+aapdhg_status aapdhg_batch_get_status(aapdhg_batch_t h, int64_t *out6) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!out6) return bfail(h, AAPDHG_ERR_INVALID, "out6 is NULL");
+    aapdhg_status s = bread_headers(h);
+    if (s != AAPDHG_OK) return s;
+    for (int32_t p = 0; p < h->nprob; ++p) {
+        const DevState *d = hdr(h, p);
+        out6[6 * p] = d->it;
+        out6[6 * p + 1] = d->n_aa;
+        out6[6 * p + 2] = d->n_pd;
+        out6[6 * p + 3] = d->n_lsfail;
+        out6[6 * p + 4] = d->done != 0;
+        out6[6 * p + 5] = d->error != 0;
+    }
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_profile_kernels(aapdhg_batch_t h, int32_t enable) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    BCK(h, cudaStreamSynchronize(h->stream));
+    bcollect(h);
+    h->prof_on = enable != 0;
+    for (int k = 0; k < BK_N; ++k) { h->prof_ms[k] = 0; h->prof_n[k] = 0; }
+    h->launches = 0;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, int64_t *launches,
+                                              double *total_ms) {
+    if (!h || !launches || !total_ms) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    BCK(h, cudaStreamSynchronize(h->stream));
+    bcollect(h);
+    if (kind == -1) { *launches = h->launches; *total_ms = 0.0; return AAPDHG_OK; }
+    if (kind < 0 || kind >= BK_N) return bfail(h, AAPDHG_ERR_INVALID, "unknown kernel kind");
+    *launches = h->prof_n[kind];
+    *total_ms = h->prof_ms[kind];
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_device_bytes(aapdhg_batch_t h, int64_t *bytes) {
+    if (!h || !bytes) return AAPDHG_ERR_INVALID;
+    *bytes = h->bytes;
+    return AAPDHG_OK;
+}
+
+const char *aapdhg_batch_last_error(aapdhg_batch_t h) {
+    if (!h) return g_batch_create_err.c_str();
+    return h->err.c_str();
+}
+
+void aapdhg_batch_destroy(aapdhg_batch_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    bdrop_graphs(h);
+    for (auto e : h->ev) cudaEventDestroy(e);
+    for (auto &a : h->allocs) raw_free(a.p);
+    h->allocs.clear();
+    if (h->hdr_host) cudaFreeHost(h->hdr_host);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+}  // extern "C"

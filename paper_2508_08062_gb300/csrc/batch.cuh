@@ -1,0 +1,447 @@
+// Batched AA-PDHG / FAA-PDHG: many independent LPs advanced together.
+//
+// The batch is packed as one block-diagonal LP: K = diag(K_1, ..., K_P), the
+// variables of all problems first (problem after problem), then their
+// constraints, each problem's two ranges padded to multiples of 4 with inert
+// elements (a variable fixed at 0 with zero cost, an empty '=' row with
+// q = 0), which stay 0 and add nothing to any sum.  Each problem keeps the
+// single-LP row order (longest first) and the single-LP slices, so every row
+// of T(u) is computed exactly as for that LP alone; the slices of all
+// problems are ordered by width across the batch.
+//
+// All problems share one iterate parity: UP[e].comp[cur] holds u^k of every
+// problem, with cur the parity of the batch's iteration counter.  Everything
+// else is per problem, in its own DevState: its step sizes, its iteration
+// count, its Anderson memory (the same slot-major rings, restricted to its
+// elements), its safeguard and solve, its KKT test and stop flag.  A problem
+// whose state says "not started" forms u^1 = T u^0 and g^0 in the iteration
+// in which it joins; a problem that has converged or failed is skipped by
+// every kernel (its two iterate components are made equal when it stops, so
+// the parity no longer matters to it).
+//
+// Kernels of one iteration (the half-steps reuse the single-LP task loop):
+//   k_xstep_b / k_ystep_b  the PDHG half-steps with per-problem tau, sigma;
+//                          on KKT iterations the KKT terms of u^k per element;
+//   k_kkt_b                per-problem KKT of u^k (Remark on termination) and
+//                          the stop test (KKT iterations only);
+//   k_memory_b             per chunk of a problem's elements: the memory pass
+//                          plus ||g^k||^2; the block whose chunk of a problem
+//                          arrives last reduces that problem's partials and
+//                          runs its safeguard and m x m work;
+//   k_mix_b                the AA mix of the problems whose step was accepted.
+#pragma once
+#include "anderson.cuh"
+#include "common.cuh"
+#include "spmv.cuh"
+
+namespace aap {
+
+constexpr int BCHUNK = 8192;          // elements per chunk of a problem (multiple of 4)
+constexpr int NBV = MAXM + 4;         // chunk partial columns: Gram row, ||dg||^2, <dg,g>, ||du||^2, ||g||^2
+
+template <typename V> struct BatchView {
+    int32_t nprob;
+    int64_t n_tot, m_tot;             // variables and constraints of all problems (padded)
+    const double *tau, *sigma;        // per problem
+    DevState *stb;                    // per problem
+    V *kterm;                         // KKT terms: 3 arrays over variables, then 2 over constraints
+    int32_t nchunk;
+    const int4 *chunk;                // chunk -> (problem, first element, length, 0: x part / 1: y part)
+    const int32_t *pchunk0;           // problem -> first chunk (nprob + 1 entries)
+    double *cpart;                    // nchunk * NBV chunk partials
+    uint32_t *pcnt;                   // per-problem arrival counters (self-resetting)
+    const double *pnorm;              // per problem: ||q||, ||c|| of the caller's LP
+};
+
+__device__ __forceinline__ bool stopped(const DevState *s) { return (s->done | s->error) != 0; }
+
+// --------------------------------------------------------------------------
+// Half-step epilogues (eq. pdhg per row, step sizes of the row's problem)
+// --------------------------------------------------------------------------
+template <typename V, bool KKT> struct EpiXB {
+    typedef typename Vec2<V>::T V2;
+    struct Pre { V2 pr; V c, l, u, tau; int keep; };
+    static constexpr bool kRowOrder = false;
+    const Prob<V> &P;
+    const BatchView<V> &B;
+    int cur, mode;
+    __device__ __forceinline__ bool skip(int p) const {
+        return mode != MODE_EVAL && stopped(B.stb + p);
+    }
+    __device__ __forceinline__ Pre pre(int j, int p) const {
+        return Pre{P.UP[j], __ldg(P.c + j), __ldg(P.lo + j), __ldg(P.hi + j), (V)__ldg(B.tau + p),
+                   (int)stopped(B.stb + p)};
+    }
+    __device__ __forceinline__ void operator()(int j, const Pre &in, const V (&s)[1]) {
+        V2 pr = in.pr;
+        const V x = comp<V>(pr, cur);
+        const V r = in.c - s[0];
+        V xh = x;                                      // a stopped problem keeps its iterate
+        if (!in.keep) {
+            xh = x - in.tau * r;
+            xh = xh < in.l ? in.l : (xh > in.u ? in.u : xh);
+        }
+        if (cur) pr.x = xh; else pr.y = xh;
+        P.UP[j] = pr;
+        if (KKT) {
+            // lambda = P_Lambda(c - K'y) (eq. lambda-case), as in the single-LP epilogue
+            const bool lf = isfinite(in.l), uf = isfinite(in.u);
+            V lamj;
+            if (!lf && !uf) lamj = V(0);
+            else if (!lf) lamj = r < V(0) ? r : V(0);
+            else if (!uf) lamj = r > V(0) ? r : V(0);
+            else lamj = r;
+            V d = r - lamj;
+            if (P.sc_x) d *= __ldg(P.sc_x + j);
+            V lt = V(0);
+            if (lamj > V(0)) lt = in.l * lamj;
+            else if (lamj < V(0)) lt = in.u * lamj;
+            B.kterm[j] = d * d;
+            B.kterm[B.n_tot + j] = lt;
+            B.kterm[2 * B.n_tot + j] = in.c * x;
+        }
+    }
+};
+
+template <typename V, bool KKT> struct EpiYB {
+    typedef typename Vec2<V>::T V2;
+    struct Pre { V2 pr; V q, l, sigma; int keep; };
+    static constexpr bool kRowOrder = false;
+    const Prob<V> &P;
+    const BatchView<V> &B;
+    int cur, mode;
+    __device__ __forceinline__ bool skip(int p) const {
+        return mode != MODE_EVAL && stopped(B.stb + p);
+    }
+    __device__ __forceinline__ Pre pre(int i, int p) const {
+        return Pre{P.UP[P.n + i], __ldg(P.q + i), __ldg(P.lo + P.n + i), (V)__ldg(B.sigma + p),
+                   (int)stopped(B.stb + p)};
+    }
+    __device__ __forceinline__ void operator()(int i, const Pre &in, const V (&t)[KKT ? 2 : 1]) {
+        V2 pr = in.pr;
+        const V y = comp<V>(pr, cur);
+        V yh = y;
+        if (!in.keep) {
+            yh = y + in.sigma * (in.q - t[0]);
+            yh = yh < in.l ? in.l : yh;
+        }
+        if (cur) pr.x = yh; else pr.y = yh;
+        P.UP[P.n + i] = pr;
+        if (KKT) {
+            V p = in.q - t[1];
+            if (in.l == V(0) && p < V(0)) p = V(0);
+            if (P.sc_y) p *= __ldg(P.sc_y + i);
+            B.kterm[3 * B.n_tot + i] = p * p;
+            B.kterm[3 * B.n_tot + B.m_tot + i] = in.q * y;
+        }
+    }
+};
+
+template <typename V, bool KKT>
+__global__ void __launch_bounds__(BLOCK) k_xstep_b(Prob<V> P, BatchView<V> B, int cur, int mode) {
+    GatherY<V> gat{reinterpret_cast<const V *>(P.UP + P.n) + cur};
+    EpiXB<V, KKT> epi{P, B, cur, mode};
+    const int warp = threadIdx.x >> 5;
+    const int64_t ntask = P.KT.ntasks();
+    for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
+        const int64_t t = vb * WARPS + warp;
+        if (t < ntask) run_task<V, 1>(P.KT, t, gat, epi);
+    }
+}
+
+template <typename V, bool KKT>
+__global__ void __launch_bounds__(BLOCK) k_ystep_b(Prob<V> P, BatchView<V> B, int cur, int mode) {
+    GatherXZ<V, KKT> gat{P.UP, cur};
+    EpiYB<V, KKT> epi{P, B, cur, mode};
+    const int warp = threadIdx.x >> 5;
+    const int64_t ntask = P.K.ntasks();
+    for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
+        const int64_t t = vb * WARPS + warp;
+        if (t < ntask) run_task<V, KKT ? 2 : 1>(P.K, t, gat, epi);
+    }
+}
+
+// Arrival of one chunk of a problem with `nchunks` chunks: true in the block
+// whose chunk arrives last (which then owns the problem's reduction).
+__device__ __forceinline__ bool last_chunk(uint32_t *cnt, int nchunks) {
+    __shared__ bool is_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        is_last = atomicAdd(cnt, 1u) == (unsigned)(nchunks - 1);
+        if (is_last) *cnt = 0u;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last;
+}
+
+// red[k] = sum over chunks [c0, c1) of column k of cpart, fixed order, for
+// the columns set in `active`; one warp per column.
+__device__ __forceinline__ void reduce_chunks(const double *cpart, int c0, int c1, int ncol,
+                                              double *red, unsigned long long active) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int k = warp; k < ncol; k += WARPS) {
+        if (!((active >> k) & 1ull)) continue;
+        double v = 0.0;
+        for (int c = c0 + lane; c < c1; c += 32) v += __ldcg(cpart + (int64_t)c * NBV + k);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) red[k] = v;
+    }
+    __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// Per-problem KKT of u^k (Remark on termination conditions) and, in mode
+// ITER, the stop test KKT <= tol.  Grid: one block per chunk.
+// --------------------------------------------------------------------------
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_kkt_b(BatchView<V> B, double tol, int mode) {
+    const int4 ch = B.chunk[blockIdx.x];
+    const int p = ch.x;
+    DevState *st = B.stb + p;
+    if (mode != MODE_EVAL && (stopped(st) || !st->init_done)) return;
+    Acc<V> a[5];
+    const int64_t e1 = (int64_t)ch.y + ch.z;
+    if (ch.w == 0) {
+        for (int64_t j = ch.y + threadIdx.x; j < e1; j += BLOCK) {
+            a[0].add(B.kterm[j]);
+            a[1].add(B.kterm[B.n_tot + j]);
+            a[2].add(B.kterm[2 * B.n_tot + j]);
+        }
+    } else {
+        for (int64_t e = ch.y + threadIdx.x; e < e1; e += BLOCK) {
+            const int64_t i = e - B.n_tot;
+            a[3].add(B.kterm[3 * B.n_tot + i]);
+            a[4].add(B.kterm[3 * B.n_tot + B.m_tot + i]);
+        }
+    }
+    __shared__ double sh[WARPS * 5];
+    block_reduce_store<V, 5>(a, sh, B.cpart + (int64_t)blockIdx.x * NBV);
+    const int c0 = B.pchunk0[p], c1 = B.pchunk0[p + 1];
+    if (!last_chunk(B.pcnt + p, c1 - c0)) return;
+    __shared__ double red[NBV];
+    reduce_chunks(B.cpart, c0, c1, 5, red, 0x1full);
+    if (threadIdx.x != 0) return;
+    const double dres2 = red[0], lam = red[1], cx = red[2], pres2 = red[3], qy = red[4];
+    const double dobj = qy + lam, pobj = cx;
+    double out[6];
+    out[0] = sqrt(pres2) / (1.0 + B.pnorm[2 * p]);
+    out[1] = sqrt(dres2) / (1.0 + B.pnorm[2 * p + 1]);
+    out[2] = fabs(dobj - pobj) / (1.0 + fabs(dobj) + fabs(pobj));
+    out[3] = fmax(out[0], fmax(out[1], out[2]));
+    out[4] = pobj;
+    out[5] = dobj;
+    for (int k = 0; k < 6; ++k) st->kkt[k] = out[k];
+    st->kkt_valid = 1;
+    if (mode == MODE_ITER) {
+        if (!isfinite(out[3])) st->error = 1;
+        else if (out[3] <= tol) st->done = 1;
+    }
+}
+
+// --------------------------------------------------------------------------
+// Memory pass, ||g^k|| and the per-problem m x m work.  Grid: one block per
+// chunk.  A problem that stopped at this iteration's KKT test (done == 1) has
+// its iterate copied into both components instead (done becomes 2).
+// --------------------------------------------------------------------------
+template <typename V, int MC>
+__global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, MethodParams mp, int cur) {
+    constexpr int W = 16 / sizeof(V);
+    typedef typename Vec2<V>::T V2;
+    const int4 ch = B.chunk[blockIdx.x];
+    const int p = ch.x;
+    DevState *st = B.stb + p;
+    if (st->error || st->done == 2) return;
+    const int c0 = B.pchunk0[p], c1 = B.pchunk0[p + 1];
+    const int64_t e0 = ch.y, e1 = (int64_t)ch.y + ch.z;
+    if (st->done) {
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += BLOCK) {
+            V2 pr = P.UP[e];
+            if (cur) pr.x = pr.y; else pr.y = pr.x;
+            P.UP[e] = pr;
+        }
+        if (last_chunk(B.pcnt + p, c1 - c0) && threadIdx.x == 0) st->done = 2;
+        return;
+    }
+    const bool init = !st->init_done;
+    const int M = (mp.method == 0) ? 0 : mp.mem;
+    __shared__ int s_old[NSLOT];
+    __shared__ int64_t s_off[NSLOT];
+    __shared__ int s_nold, s_new, s_prev_acc;
+    __shared__ double sh[WARPS * (MC + 4)];
+    if (threadIdx.x == 0) {
+        int t = 0;
+        if (!init) {
+            const int cnt = st->count;
+            const int drop = (M > 0 && cnt == M) ? 1 : 0;
+            for (int i = drop; i < cnt; ++i) s_old[t++] = st->list[i];
+        }
+        s_nold = t;
+        s_new = init ? 0 : st->free_slot;
+        s_prev_acc = init ? 0 : st->accept;
+    }
+    __syncthreads();
+    if (threadIdx.x < NSLOT)
+        s_off[threadIdx.x] = (int64_t)s_old[threadIdx.x < s_nold ? threadIdx.x : 0] * P.Npad;
+    __syncthreads();
+    const int nold = s_nold, sn = s_new;
+    const bool prev_acc = s_prev_acc != 0;
+
+    // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2; MC+3: ||g||^2
+    Acc<V> acc[MC + 4];
+    const int64_t stride = (int64_t)BLOCK * W;
+    if (M > 0 && init) {
+        // g^0 = u^1 - u^0 (u^1 = T u^0 was just written into the other component)
+        const V *UPs = reinterpret_cast<const V *>(P.UP);
+        for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride) {
+            const Pack<V, W> pa = ld<V, W>(UPs + 2 * e), pb = ld<V, W>(UPs + 2 * e + W);
+            Pack<V, W> gk;
+#pragma unroll
+            for (int i = 0; i < W; ++i) {
+                const int i0 = 2 * i, i1 = 2 * i + 1;
+                const V a0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
+                const V a1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
+                gk.v[i] = (cur ? a0 : a1) - (cur ? a1 : a0);
+                acc[MC + 3].add_sq(gk.v[i]);
+            }
+            aap::st<V, W>(P.g + e, gk);
+        }
+    } else if (M > 0) {
+        V *DGn = P.DG + (int64_t)sn * P.Npad;
+        V *Wn = P.W + (int64_t)sn * P.Npad;
+        const V beta = (V)mp.beta;
+        for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride)
+            memory_elems<V, MC, W, true>(P, e, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
+    }
+    {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+        for (int s = 0; s < MC + 4; ++s) {
+            if (s < nold || s >= MC) {
+                acc[s].warp_allreduce();
+                if (lane == 0) sh[warp * (MC + 4) + s] = acc[s].value();
+            }
+        }
+        __syncthreads();
+        for (int s = threadIdx.x; s < MC + 4; s += BLOCK) {
+            if (s < nold || s >= MC) {
+                double v = 0.0;
+                for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 4) + s];
+                B.cpart[(int64_t)blockIdx.x * NBV + (s < MC ? s : MAXM + (s - MC))] = v;
+            }
+        }
+    }
+    if (!last_chunk(B.pcnt + p, c1 - c0)) return;
+
+    // ---- this problem's reduction and m x m work (one block) --------------
+    __shared__ double redb[NBV];
+    __shared__ double red[MC + 3];
+    __shared__ SolveSmem sm;
+    unsigned long long active = 0xFull << MAXM;
+    for (int t = 0; t < nold; ++t) active |= 1ull << t;
+    if (M > 0) reduce_chunks(B.cpart, c0, c1, NBV, redb, active);
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    const double gn = M > 0 ? sqrt(redb[MAXM + 3]) : 0.0;
+    if (init) {
+        if (lane == 0) {
+            if (!isfinite(gn)) st->error = 1;
+            st->g0 = gn;
+            st->gnorm = gn;
+            st->count = 0;
+            st->new_slot = 0;
+            st->free_slot = 0;
+            st->accept = 0;   // u^1 = T u^0 behaves as a PDHG step: du^0 = g^0
+            st->use_count = 0;
+            st->it = 0;
+            st->init_done = 1;
+        }
+        return;
+    }
+    if (!isfinite(gn)) {
+        if (lane == 0) st->error = 1;
+        return;
+    }
+    for (int t = lane; t < nold; t += 32) red[t] = redb[t];
+    if (lane == 0 && M > 0) {
+        red[MC] = redb[MAXM];
+        red[MC + 1] = redb[MAXM + 1];
+        red[MC + 2] = redb[MAXM + 2];
+    }
+    bool want = false;
+    if (mp.method != 0 && M > 0)
+        want = gn <= mp.D * st->g0 * pow((double)st->n_aa / mp.c_div + 1.0, -(1.0 + mp.eps));
+    if (lane == 0) {
+        st->gnorm = gn;
+        st->want_aa = want ? 1 : 0;
+    }
+    __syncwarp();
+    const Trace none{0, nullptr, nullptr, nullptr, nullptr};
+    memory_finalize<MC>(st, mp, M, s_old, nold, sn, red, sm, none);
+}
+
+// --------------------------------------------------------------------------
+// AA mix of the problems whose step was accepted.  Grid: one block per chunk.
+// --------------------------------------------------------------------------
+template <typename V, int MC>
+__global__ void __launch_bounds__(BLOCK) k_mix_b(Prob<V> P, BatchView<V> B, MethodParams mp, int cur) {
+    constexpr int W = 16 / sizeof(V);
+    const int4 ch = B.chunk[blockIdx.x];
+    const DevState *st = B.stb + ch.x;
+    if (stopped(st) || !st->init_done || !st->accept) return;
+    const int64_t e0 = ch.y, e1 = (int64_t)ch.y + ch.z;
+    __shared__ V s_gam[MC];
+    __shared__ int64_t s_off[MC];
+    if (threadIdx.x < MC) {
+        const bool on = threadIdx.x < st->use_count;
+        s_gam[threadIdx.x] = on ? (V)st->gamma[threadIdx.x] : V(0);
+        s_off[threadIdx.x] = (int64_t)(on ? st->use[threadIdx.x] : 0) * P.Npad;
+    }
+    __syncthreads();
+    const int k = st->use_count;
+    V *Wf = P.W + (int64_t)st->free_slot * P.Npad;
+    const V beta = (V)mp.beta;
+    for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += (int64_t)BLOCK * W)
+        mix_elems<V, MC, W>(P, e, cur, beta, s_gam, s_off, k, Wf);
+}
+
+// Per-problem status for the host: (iterations, AA steps, PDHG steps, done,
+// error, started).
+__global__ void k_batch_status(const DevState *stb, int nprob, int64_t *out) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x) {
+        out[6 * p] = stb[p].it;
+        out[6 * p + 1] = stb[p].n_aa;
+        out[6 * p + 2] = stb[p].n_pd;
+        out[6 * p + 3] = stb[p].done;
+        out[6 * p + 4] = stb[p].error;
+        out[6 * p + 5] = stb[p].init_done;
+    }
+}
+
+// A new solve call re-tests every problem against its own tolerance.
+__global__ void k_batch_clear_done(DevState *stb, int nprob) {
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nprob; p += gridDim.x * blockDim.x)
+        stb[p].done = 0;
+}
+
+// Power iteration per problem: out[s] = ||v||^2 over segment [off[s], off[s+1])
+// (one block per segment, fixed order), and v scaled by 1 / sqrt(out[s]) there.
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_seg_sumsq(const V *v, const int64_t *off, double *out) {
+    const int s = blockIdx.x;
+    Acc<V> a[1];
+    for (int64_t e = off[s] + threadIdx.x; e < off[s + 1]; e += BLOCK) a[0].add_sq(v[e]);
+    __shared__ double sh[WARPS];
+    block_reduce_store<V, 1>(a, sh, out + s);
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_seg_scale(V *v, const int64_t *off, const double *ss) {
+    const int s = blockIdx.x;
+    const V f = (V)(ss[s] > 0 ? 1.0 / sqrt(ss[s]) : 0.0);
+    for (int64_t e = off[s] + threadIdx.x; e < off[s + 1]; e += BLOCK) v[e] *= f;
+}
+
+}  // namespace aap

@@ -81,6 +81,7 @@ struct DevState {
     int64_t n_lsfail;      // AA steps rejected by a failed factorisation
     int32_t done;          // KKT <= tol reached at the current iterate
     int32_t error;         // non-zero: NaN/Inf met (iterate left unchanged)
+    int32_t init_done;     // u^1 = T u^0 and g^0 formed
     int32_t want_aa;       // safeguard passed this iteration
     int32_t accept;        // AA step taken this iteration
     int32_t count;         // columns in the memory
@@ -97,7 +98,6 @@ struct DevState {
     double gnorm;          // ||g^k||
     double kkt[6];         // r_p, r_d, r_g, KKT, c'x, dual objective at u^k
     int32_t kkt_valid;
-    int32_t init_done;     // u^1 = T u^0 and g^0 formed
     uint32_t cnt_spmv;     // last-block counter of the y-step
     uint32_t cnt_ring;     // last-block counter of the memory pass
     uint32_t cnt_norm;     // last-block counter of the norm kernels
@@ -126,13 +126,17 @@ struct Trace {
 };
 
 // One sparse matrix (K or K') with rows renumbered longest first, in two parts:
-//  - rows [0, n_long), longer than SELL_MAX entries: CSR, cut into chunks of
-//    at most LONG_CHUNK entries, one warp task per chunk (a row with several
-//    chunks is finished by the warp whose chunk arrives last);
-//  - rows [n_long, rows): SELL-32 slices of 32 consecutive rows stored column
-//    by column (entry t of the 32 rows contiguous), padded with zero entries
-//    (column 0, value 0) to the slice's longest row; one warp task per
-//    SLICES_PER_TASK consecutive slices, lane = row of each slice.
+//  - n_long rows longer than SELL_MAX entries ("long rows", numbered by a
+//    long-row id): CSR, cut into chunks of at most LONG_CHUNK entries, one
+//    warp task per chunk (a row with several chunks is finished by the warp
+//    whose chunk arrives last);
+//  - the other rows: SELL-32 slices of up to 32 consecutive rows stored
+//    column by column (entry t of the rows contiguous), padded with zero
+//    entries (column 0, value 0) to the slice's longest row; one warp task
+//    per SLICES_PER_TASK slices, lane = row of each slice.
+// Every chunk and slice names its rows and the problem they belong to, so one
+// matrix may hold the block-diagonal K of a batch of LPs, its slices ordered
+// by width across all problems (a single LP is problem 0).
 // The full CSR (rp, ci, val) is kept for the set-up kernels.
 template <typename V> struct CSRView {
     int32_t rows;
@@ -140,13 +144,14 @@ template <typename V> struct CSRView {
     const int32_t *ci;
     const V *val;
     int32_t n_long, n_chunks, n_slices;
-    const int32_t *chunk_row;     // chunk -> row
-    const int32_t *row_chunk0;    // split row -> first chunk (n_long + 1 entries)
-    const int2 *slice_meta;       // slice -> (offset of its first entry in sell_*, width)
+    const int4 *chunk_meta;       // chunk -> (row, long-row id, problem, 0)
+    const int32_t *row_chunk0;    // long-row id -> first chunk (n_long + 1 entries)
+    const int4 *slice_meta;       // slice -> (offset of its first entry in sell_*, width,
+                                  //           first row, rows | problem << 6)
     const int32_t *sell_ci;
     const V *sell_val;
     V *chunk_part;                // n_chunks * 2 partial sums of split rows
-    uint32_t *chunk_cnt;          // n_long arrival counters (self-resetting)
+    uint32_t *chunk_cnt;          // arrival counters by long-row id (self-resetting)
     __host__ __device__ int64_t ntasks() const {
         return (int64_t)n_chunks + (n_slices + SLICES_PER_TASK - 1) / SLICES_PER_TASK;
     }

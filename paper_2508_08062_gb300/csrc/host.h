@@ -1,0 +1,104 @@
+// Host-side pieces shared by the single-LP and the batched runtimes: input
+// validation, the longest-first renumbering of K and K', the chunk / SELL-32
+// layout of a (possibly block-diagonal) matrix and its upload.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace aaph {
+
+struct HostCSR {
+    int32_t rows = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double> val;
+};
+
+// Rows [row0, row0 + rows) of one problem, sorted longest first.
+struct RowSeg {
+    int32_t row0, rows, pid;
+};
+
+// Device-side tables of one matrix built on the host: chunk tables of the long
+// rows and the SELL-32 slices of the others.
+struct LayoutHost {
+    int32_t n_long = 0, n_chunks = 0, n_slices = 0;
+    std::vector<int4> chunk_meta;          // (row, long-row id, problem, 0)
+    std::vector<int32_t> row_chunk0;       // long-row id -> first chunk
+    std::vector<int4> slice_meta;          // (offset, width, first row, rows | problem << 6)
+    std::vector<int32_t> sell_ci;
+    std::vector<double> sell_val;
+};
+
+// Layout of A whose rows form the segments `segs` (each longest first): the
+// leading rows of a segment longer than SELL_MAX become long rows, the rest
+// slices of up to 32 rows that never cross a segment.  Slices are ordered by
+// width, widest first, across all segments (stable, so a single segment keeps
+// its row order).  Returns false when the SELL storage would pass 2^31 entries.
+bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L);
+
+// Internal CSR of K (rows renumbered longest-first, columns mapped to the
+// internal variable order) and of K' (likewise), column indices ascending
+// within each row.  perm_x / perm_y map internal to caller order.
+void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, const double *val,
+                    std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
+                    HostCSR &KT);
+
+// Checks of one LP in the C ABI's input form; returns an empty string when it
+// is valid, else the reason.
+std::string validate_lp(int32_t m, int32_t n, int64_t nnz, const int64_t *rp, const int32_t *ci,
+                        const double *val, const int8_t *sense, const double *q, const double *c,
+                        const double *lb, const double *ub);
+
+// Device memory through the allocator installed by aapdhg_set_allocator (or
+// cudaMalloc / cudaFree).
+void *raw_alloc(size_t bytes);
+void raw_free(void *p);
+
+// Upload A and its layout into `view` (values rounded to V); `alloc(bytes)`
+// returns tracked device memory.  Synchronises `s` (the sources are pageable).
+template <typename V, class Alloc>
+bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Alloc &&alloc,
+                cudaStream_t s) {
+    bool ok = true;
+    auto put = [&](const auto *src, size_t count) {
+        typedef std::remove_cv_t<std::remove_pointer_t<decltype(src)>> T;
+        T *d = (T *)alloc(sizeof(T) * std::max<size_t>(count, 1));
+        if (!d) { ok = false; return (T *)nullptr; }
+        if (count && cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            ok = false;
+        return d;
+    };
+    auto to_v = [](const std::vector<double> &a) {
+        std::vector<V> o(a.size());
+        for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
+        return o;
+    };
+    view.rows = A.rows;
+    view.rp = put(A.rp.data(), A.rp.size());
+    view.ci = put(A.ci.data(), A.ci.size());
+    const std::vector<V> v = to_v(A.val), sv = to_v(L.sell_val);
+    view.val = put(v.data(), v.size());
+    view.n_long = L.n_long;
+    view.n_chunks = L.n_chunks;
+    view.n_slices = L.n_slices;
+    view.chunk_meta = put(L.chunk_meta.data(), L.chunk_meta.size());
+    view.row_chunk0 = put(L.row_chunk0.data(), L.row_chunk0.size());
+    view.slice_meta = put(L.slice_meta.data(), L.slice_meta.size());
+    view.sell_ci = put(L.sell_ci.data(), L.sell_ci.size());
+    view.sell_val = put(sv.data(), sv.size());
+    view.chunk_part = (V *)alloc(sizeof(V) * 2 * std::max(1, L.n_chunks));
+    view.chunk_cnt = (uint32_t *)alloc(sizeof(uint32_t) * std::max(1, L.n_long));
+    if (!view.chunk_part || !view.chunk_cnt) ok = false;
+    else if (cudaMemsetAsync(view.chunk_cnt, 0, sizeof(uint32_t) * std::max(1, L.n_long), s) != cudaSuccess)
+        ok = false;
+    if (cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+    return ok;
+}
+
+}  // namespace aaph

@@ -55,14 +55,34 @@ __global__ void k_scale_matrix(CSRView<V> A, const V *drow, const V *dcol) {
     }
     V *sv = const_cast<V *>(A.sell_val);
     for (int64_t s = w0; s < A.n_slices; s += warps) {
-        const int2 meta = A.slice_meta[s];
-        const int64_t r = A.n_long + s * 32 + lane;
-        if (r >= A.rows) continue;
+        const int4 meta = A.slice_meta[s];
+        const int64_t r = meta.z + lane;
+        if (lane >= (meta.w & 63)) continue;
         const V fr = drow[r];
         for (int t = 0; t < meta.y; ++t) {
             const int64_t q = (int64_t)meta.x + (int64_t)t * 32 + lane;
             sv[q] = sv[q] * fr * dcol[A.sell_ci[q]];    // padding entries are 0 and stay 0
         }
+    }
+}
+
+// D-hat of the Remark on its construction (mode 1) or the identity (mode 0):
+// per row of K' (a variable) and per row of K (a constraint),
+// sqrt(max(max |entry|, 1e-10)).  One warp per row, lanes striding its entries.
+template <typename V>
+__global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mode, V *dh) {
+    const int64_t N = (int64_t)n + m;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t e = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); e < N; e += warps) {
+        if (mode == 0) { if (lane == 0) dh[e] = V(1); continue; }
+        const CSRView<V> &A = e < n ? KT : K;
+        const int32_t r = (int32_t)(e < n ? e : e - n);
+        double mx = 0.0;
+        for (int32_t k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) mx = fmax(mx, fabs((double)A.val[k]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) dh[e] = (V)sqrt(fmax(mx, 1e-10));
     }
 }
 

@@ -26,9 +26,15 @@
 namespace aap {
 
 // Process warp task t of matrix A.  gather(col, val, acc) folds one entry
-// into the NACC per-lane partial sums.  The epilogue has two halves:
-// epi.pre(row) loads the row's own inputs (issued before the sum, since they
-// do not depend on it) and epi(row, pre, sums) finishes the row on one lane.
+// into the NACC per-lane partial sums.  The epilogue has three parts:
+// epi.skip(problem) says that a problem's rows are left untouched (a batch
+// member that has stopped), epi.pre(row, problem) loads the row's own inputs
+// (issued before the sum, since they do not depend on it) and
+// epi(row, pre, sums) finishes the row on one lane.  Epi::kRowOrder: the
+// slices are those of one LP in row order (slice q holds rows n_long + 32q
+// on), so a lane's row is known without the slice's metadata and its inputs
+// are requested together with that metadata; otherwise (a batch) the row
+// comes from the metadata.
 template <typename V, int NACC, class Gather, class Epi>
 __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather &gather, Epi &epi) {
     typedef typename Epi::Pre Pre;
@@ -39,13 +45,15 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = V(0);
         const int chunk = (int)t;
-        const int r = __ldg(A.chunk_row + chunk);
-        const int c0 = __ldg(A.row_chunk0 + r);
-        const int nch = __ldg(A.row_chunk0 + r + 1) - c0;
+        const int4 cm = __ldg(A.chunk_meta + chunk);
+        const int r = cm.x, lr = cm.y;
+        if (epi.skip(cm.z)) return;
+        const int c0 = __ldg(A.row_chunk0 + lr);
+        const int nch = __ldg(A.row_chunk0 + lr + 1) - c0;
         const int k0 = __ldg(A.rp + r) + (chunk - c0) * LONG_CHUNK;
         const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
         Pre pre;
-        if (nch == 1 && lane == 0) pre = epi.pre(r);
+        if (nch == 1 && lane == 0) pre = epi.pre(r, cm.z);
         for (int kb = k0 + lane; kb < k1; kb += 32 * LOADS) {
             int ci[LOADS];
             V va[LOADS];
@@ -72,19 +80,19 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
 #pragma unroll
             for (int a = 0; a < NACC; ++a) A.chunk_part[(int64_t)chunk * 2 + a] = acc[a];
             __threadfence();
-            last = (atomicAdd(A.chunk_cnt + r, 1u) == (unsigned)(nch - 1));
+            last = (atomicAdd(A.chunk_cnt + lr, 1u) == (unsigned)(nch - 1));
         }
         last = __shfl_sync(0xffffffffu, last, 0);
         if (last && lane == 0) {
             __threadfence();
-            pre = epi.pre(r);
+            pre = epi.pre(r, cm.z);
             V tot[NACC];
 #pragma unroll
             for (int a = 0; a < NACC; ++a) tot[a] = V(0);
             for (int c = c0; c < c0 + nch; ++c)
 #pragma unroll
                 for (int a = 0; a < NACC; ++a) tot[a] += __ldcg(A.chunk_part + (int64_t)c * 2 + a);
-            A.chunk_cnt[r] = 0u;
+            A.chunk_cnt[lr] = 0u;
             epi(r, pre, tot);
         }
         return;
@@ -97,22 +105,29 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
     const int sl0 = (int)(t - A.n_chunks) * G;
     int2 meta[G];
     int r[G];
+    bool valid[G];
     Pre pre[G];
     V acc[G][NACC];
     int wmax = 0;
 #pragma unroll
     for (int g = 0; g < G; ++g) {
         const bool on = sl0 + g < A.n_slices;
-        meta[g] = on ? __ldg(A.slice_meta + sl0 + g) : make_int2(0, 0);
-        r[g] = A.n_long + (sl0 + g) * 32 + lane;
-        if (r[g] < A.rows) pre[g] = epi.pre(r[g]);
+        const int4 m4 = on ? __ldg(A.slice_meta + sl0 + g) : make_int4(0, 0, 0, 0);
+        if constexpr (Epi::kRowOrder) {
+            r[g] = A.n_long + 32 * (sl0 + g) + lane;
+            valid[g] = r[g] < A.rows;
+            if (valid[g]) pre[g] = epi.pre(r[g], 0);
+            meta[g] = make_int2(m4.x + lane, valid[g] ? m4.y : 0);
+        } else {
+            const int pid = m4.w >> 6;
+            valid[g] = lane < (m4.w & 63) && !epi.skip(pid);
+            meta[g] = make_int2(m4.x + lane, valid[g] ? m4.y : 0);
+            r[g] = m4.z + lane;
+            if (valid[g]) pre[g] = epi.pre(r[g], pid);
+        }
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[g][a] = V(0);
-    }
-#pragma unroll
-    for (int g = 0; g < G; ++g) {
-        meta[g].x += lane;
-        wmax = max(wmax, meta[g].y);
+        wmax = max(wmax, m4.y);
     }
     for (int t0 = 0; t0 < wmax; t0 += B) {
         int ci[G][B];
@@ -134,7 +149,7 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
     }
 #pragma unroll
     for (int g = 0; g < G; ++g)
-        if (r[g] < A.rows) epi(r[g], pre[g], acc[g]);
+        if (valid[g]) epi(r[g], pre[g], acc[g]);
 }
 
 // --------------------------------------------------------------------------
@@ -150,11 +165,13 @@ template <typename V> struct GatherY {
 template <typename V, bool KKT> struct EpiX {
     typedef typename Vec2<V>::T V2;
     struct Pre { V2 pr; V c, l, u; };
+    static constexpr bool kRowOrder = true;
     const Prob<V> &P;
     V tau;
     int cur;
     Acc<V> &g2, &dres2, &lam, &cx;
-    __device__ __forceinline__ Pre pre(int j) const {
+    __device__ __forceinline__ bool skip(int) const { return false; }
+    __device__ __forceinline__ Pre pre(int j, int) const {
         return Pre{P.UP[j], __ldg(P.c + j), __ldg(P.lo + j), __ldg(P.hi + j)};
     }
     __device__ __forceinline__ void operator()(int j, const Pre &in, const V (&s)[1]) {
@@ -223,11 +240,13 @@ template <typename V, bool KKT> struct GatherXZ {
 template <typename V, bool KKT> struct EpiY {
     typedef typename Vec2<V>::T V2;
     struct Pre { V2 pr; V q, l; };
+    static constexpr bool kRowOrder = true;
     const Prob<V> &P;
     V sigma;
     int cur;
     Acc<V> &g2, &pres2, &qy;
-    __device__ __forceinline__ Pre pre(int i) const {
+    __device__ __forceinline__ bool skip(int) const { return false; }
+    __device__ __forceinline__ Pre pre(int i, int) const {
         return Pre{P.UP[P.n + i], __ldg(P.q + i), __ldg(P.lo + P.n + i)};
     }
     __device__ __forceinline__ void operator()(int i, const Pre &in, const V (&t)[KKT ? 2 : 1]) {
@@ -324,23 +343,25 @@ template <typename V> struct GatherPlain {
         acc[0] = fma(a, __ldg(x + j), acc[0]);
     }
 };
-template <typename V> struct EpiStore {
+template <typename V, bool RowOrder> struct EpiStore {
     struct Pre {};
+    static constexpr bool kRowOrder = RowOrder;
     V *y;
     Acc<V> &n2;
-    __device__ __forceinline__ Pre pre(int) const { return Pre{}; }
+    __device__ __forceinline__ bool skip(int) const { return false; }
+    __device__ __forceinline__ Pre pre(int, int) const { return Pre{}; }
     __device__ __forceinline__ void operator()(int r, const Pre &, const V (&s)[1]) {
         y[r] = s[0];
         n2.add_sq(s[0]);
     }
 };
 
-template <typename V>
+template <typename V, bool RowOrder = true>
 __global__ void __launch_bounds__(BLOCK) k_spmv_plain(CSRView<V> A, const V *x, V *y, double *part) {
     __shared__ double sh[WARPS];
     Acc<V> n2;
     GatherPlain<V> gat{x};
-    EpiStore<V> epi{y, n2};
+    EpiStore<V, RowOrder> epi{y, n2};
     const int warp = threadIdx.x >> 5;
     const int64_t ntask = A.ntasks();
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {

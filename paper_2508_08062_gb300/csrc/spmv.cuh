@@ -45,7 +45,14 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a] = V(0);
         const int chunk = (int)t;
-        const int4 cm = __ldg(A.chunk_meta + chunk);
+        int4 cm;
+        if constexpr (Epi::kRowOrder) {          // one LP: long-row id = row, problem 0
+            cm.x = __ldg(reinterpret_cast<const int *>(A.chunk_meta + chunk));
+            cm.y = cm.x;
+            cm.z = 0;
+        } else {
+            cm = __ldg(A.chunk_meta + chunk);
+        }
         const int r = cm.x, lr = cm.y;
         if (epi.skip(cm.z)) return;
         const int c0 = __ldg(A.row_chunk0 + lr);
@@ -109,25 +116,38 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
     Pre pre[G];
     V acc[G][NACC];
     int wmax = 0;
+    if constexpr (Epi::kRowOrder) {
+        // one LP: rows from the slice index, only (offset, width) loaded
 #pragma unroll
-    for (int g = 0; g < G; ++g) {
-        const bool on = sl0 + g < A.n_slices;
-        const int4 m4 = on ? __ldg(A.slice_meta + sl0 + g) : make_int4(0, 0, 0, 0);
-        if constexpr (Epi::kRowOrder) {
-            r[g] = A.n_long + 32 * (sl0 + g) + lane;
+        for (int g = 0; g < G; ++g) {
+            const bool on = sl0 + g < A.n_slices;
+            meta[g] = on ? __ldg(reinterpret_cast<const int2 *>(A.slice_meta + sl0 + g)) : make_int2(0, 0);
+            r[g] = A.n_long + (sl0 + g) * 32 + lane;
+            if (r[g] < A.rows) pre[g] = epi.pre(r[g], 0);
+#pragma unroll
+            for (int a = 0; a < NACC; ++a) acc[g][a] = V(0);
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            meta[g].x += lane;
+            wmax = max(wmax, meta[g].y);
             valid[g] = r[g] < A.rows;
-            if (valid[g]) pre[g] = epi.pre(r[g], 0);
-            meta[g] = make_int2(m4.x + lane, valid[g] ? m4.y : 0);
-        } else {
+        }
+    } else {
+        // a batch: rows and problem from the slice's metadata
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const bool on = sl0 + g < A.n_slices;
+            const int4 m4 = on ? __ldg(A.slice_meta + sl0 + g) : make_int4(0, 0, 0, 0);
             const int pid = m4.w >> 6;
             valid[g] = lane < (m4.w & 63) && !epi.skip(pid);
             meta[g] = make_int2(m4.x + lane, valid[g] ? m4.y : 0);
             r[g] = m4.z + lane;
             if (valid[g]) pre[g] = epi.pre(r[g], pid);
-        }
 #pragma unroll
-        for (int a = 0; a < NACC; ++a) acc[g][a] = V(0);
-        wmax = max(wmax, m4.y);
+            for (int a = 0; a < NACC; ++a) acc[g][a] = V(0);
+            wmax = max(wmax, m4.y);
+        }
     }
     for (int t0 = 0; t0 < wmax; t0 += B) {
         int ci[G][B];

@@ -196,6 +196,22 @@ aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable);
 aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
                                         double *total_ms);
 
+/* Autotuning of the two PDHG half-step kernels (the SpMVs of eq. pdhg; the
+ * paper has no counterpart).  They are compiled for AAPDHG_TASK_SHAPES task
+ * shapes (shape 0: two SELL slices per warp task, 8 loads in flight per lane;
+ * 1: one slice, 8 loads; 2: four slices, 8 loads), which sum every row in the
+ * same order, so the shape never changes a result.  By default the first
+ * aapdhg_iterate times every shape on the handle's matrices and keeps the
+ * fastest of each kernel.  aapdhg_autotune does that now and returns the
+ * chosen shapes and (avg_us, optional: 2 * AAPDHG_TASK_SHAPES doubles, x-step
+ * shapes then y-step shapes) the average launch time of each; it changes no
+ * run state.  aapdhg_set_task_shape fixes the two shapes (no tuning), or with
+ * (-1, -1) re-enables tuning at the next iterate; other values give
+ * AAPDHG_ERR_INVALID.                                                        */
+enum { AAPDHG_TASK_SHAPES = 3 };
+aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us);
+aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y);
+
 /* KKT residuals of a given point without any device allocation.  The paper
  * has no counterpart to this entry point; it exists for callers that cannot
  * allocate device memory when they need the residuals: code running during
@@ -322,6 +338,21 @@ aapdhg_status aapdhg_batch_reset(aapdhg_batch_t h);
 aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double tol,
                                    int32_t kkt_every, int64_t *iters_done);
 
+/* Per-problem tolerances (host array of nprob, each >= 0): problem p stops
+ * when its KKT residual is <= tol[p]; the tol argument of iterate / launch is
+ * then ignored.  NULL restores one tolerance for all.                        */
+aapdhg_status aapdhg_batch_set_tolerances(aapdhg_batch_t h, const double *tol);
+
+/* Asynchronous form of iterate: aapdhg_batch_launch enqueues n_iters batch
+ * iterations on the handle's stream and returns without waiting (the first
+ * call after create / reset / a set_* call also forms u^1 = T u^0 of every
+ * problem first).  Unlike iterate it does not re-test problems that already
+ * converged.  aapdhg_batch_poll waits for the enqueued work, reads every
+ * problem's state (then available through aapdhg_batch_get_status) and sets
+ * *all_stopped (optional) to 1 when every problem has converged or failed.    */
+aapdhg_status aapdhg_batch_launch(aapdhg_batch_t h, int64_t n_iters, double tol, int32_t kkt_every);
+aapdhg_status aapdhg_batch_poll(aapdhg_batch_t h, int32_t *all_stopped);
+
 /* Current iterates of all problems in the caller's order, concatenated as the
  * inputs (x: sum(n[p]), y: sum(m[p]); either may be NULL).                   */
 aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y);
@@ -341,9 +372,66 @@ aapdhg_status aapdhg_batch_profile_kernels(aapdhg_batch_t h, int32_t enable);
 aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, int64_t *launches,
                                               double *total_ms);
 
+/* As aapdhg_autotune / aapdhg_set_task_shape, on the packed batch.          */
+aapdhg_status aapdhg_batch_autotune(aapdhg_batch_t h, int32_t *shape_x, int32_t *shape_y,
+                                    double *avg_us);
+aapdhg_status aapdhg_batch_set_task_shape(aapdhg_batch_t h, int32_t shape_x, int32_t shape_y);
+
 aapdhg_status aapdhg_batch_device_bytes(aapdhg_batch_t h, int64_t *bytes);
 const char *aapdhg_batch_last_error(aapdhg_batch_t h);
 void aapdhg_batch_destroy(aapdhg_batch_t h);
+
+/* ===========================================================================
+ * Served stream: LPs arriving over time, solved with continuous batching.
+ *
+ * A server admits submitted LPs, as the device memory budget allows, into
+ * cohorts (batched solvers, each on its own CUDA stream) and advances all
+ * cohorts together, one chunk of kkt_every = 64 iterations per cohort per
+ * aapdhg_server_step.  Every cohort is set up as Sec. 5 describes (Ruiz x10 +
+ * Pock-Chambolle scaling, step sizes 0.9 / ||K_p|| from 100 power iterations,
+ * the given method and memory, D = 10, eps = 1, eta = 1e-10, beta = 1,
+ * c_s = 0.2, kappa = 1e8), each LP with its own tolerance; LPs whose tolerance
+ * is below 1e-5 are solved in FP64 cohorts, the others in mixed precision.
+ * An LP leaves the GPU when its cohort has finished (every member converged,
+ * failed or at the iteration cap); its time of convergence is recorded when
+ * the step that observes it ends.  The paper solves one LP at a time; this is
+ * its method applied to a stream.
+ *
+ *   create:  method, m_A as aapdhg_set_method; max_cohorts >= 1 running at
+ *            once; max_cohort_size >= 1 LPs per cohort; max_iters >= 1 per
+ *            LP; mem_budget device bytes all cohorts may hold (0: 80% of the
+ *            free device memory at create).
+ *   submit:  one LP in the form of aapdhg_create (host memory, copied), tol > 0;
+ *            returns its id.  A malformed LP (the checks of aapdhg_create) is
+ *            refused with AAPDHG_ERR_INVALID, which is not sticky; an LP larger
+ *            than the whole budget ends in state AAPDHG_REQ_REJECTED.
+ *   step:    one scheduling round (launch, admit, poll, retire); *running and
+ *            *waiting (optional) give the cohorts on the GPU and the LPs
+ *            queued after the round.
+ *   result:  state of LP `id`; times3 (optional) = {submit, admit, done} in
+ *            seconds from create (-1: not yet); x (n), y (m), kkt6 (as
+ *            aapdhg_get_kkt) and iters once the state is CONVERGED, CAPPED or
+ *            ERROR after admission.
+ * The server and its cohorts are used from one host thread.                  */
+typedef struct aapdhg_server_s *aapdhg_server_t;
+enum {
+    AAPDHG_REQ_WAITING = 0, AAPDHG_REQ_RUNNING = 1, AAPDHG_REQ_CONVERGED = 2,
+    AAPDHG_REQ_CAPPED = 3, AAPDHG_REQ_ERROR = 4, AAPDHG_REQ_REJECTED = 5
+};
+aapdhg_status aapdhg_server_create(int32_t method, int32_t m_A, int32_t max_cohorts,
+                                   int32_t max_cohort_size, int64_t max_iters,
+                                   int64_t mem_budget, aapdhg_server_t *out);
+aapdhg_status aapdhg_server_submit(aapdhg_server_t s, int32_t m, int32_t n, int64_t nnz,
+                                   const int64_t *row_ptr, const int32_t *col_idx,
+                                   const double *val, const int8_t *row_sense, const double *q,
+                                   const double *c, const double *lb, const double *ub, double tol,
+                                   int64_t *id);
+aapdhg_status aapdhg_server_step(aapdhg_server_t s, int32_t *running, int32_t *waiting);
+aapdhg_status aapdhg_server_result(aapdhg_server_t s, int64_t id, int32_t *state, double *x,
+                                   double *y, double *kkt6, int64_t *iters, double *times3);
+aapdhg_status aapdhg_server_device_bytes(aapdhg_server_t s, int64_t *bytes);
+const char *aapdhg_server_last_error(aapdhg_server_t s);
+void aapdhg_server_destroy(aapdhg_server_t s);
 
 #ifdef __cplusplus
 }

@@ -3,5 +3,5 @@
 The solver lives in the CUDA library ``libaapdhg.so`` (C ABI: ``include/aapdhg.h``);
 ``binding`` is a thin ctypes wrapper over it.  Build with ``build.build()``.
 """
-from .binding import (AA, FAA, FP64, MIXED, PDHG, AAPDHGError, BatchSolver, Solver,  # noqa: F401
-                      load, use_torch_allocator)
+from .binding import (AA, FAA, FP64, MIXED, PDHG, AAPDHGError, BatchSolver, Server,  # noqa: F401
+                      Solver, load, use_torch_allocator)

@@ -17,6 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaapdhg.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, NOT_CONVERGED = range(7)
+TASK_SHAPES = 3
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NUMERIC",
                 5: "ERR_TIMEOUT", 6: "NOT_CONVERGED"}
 ROW_EQ, ROW_GE = 0, 1
@@ -33,6 +34,11 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
            "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
+           "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_batch_autotune",
+           "aapdhg_batch_set_task_shape", "aapdhg_batch_set_tolerances", "aapdhg_batch_launch",
+           "aapdhg_batch_poll", "aapdhg_server_create", "aapdhg_server_submit",
+           "aapdhg_server_step", "aapdhg_server_result", "aapdhg_server_device_bytes",
+           "aapdhg_server_last_error", "aapdhg_server_destroy",
            "aapdhg_batch_create", "aapdhg_batch_set_steps", "aapdhg_batch_estimate_norms",
            "aapdhg_batch_set_method", "aapdhg_batch_set_scaling", "aapdhg_batch_set_start",
            "aapdhg_batch_reset", "aapdhg_batch_iterate", "aapdhg_batch_get_iterate",
@@ -40,7 +46,7 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_batch_get_kernel_profile", "aapdhg_batch_device_bytes",
            "aapdhg_batch_last_error", "aapdhg_batch_destroy")
 NO_STATUS = ("aapdhg_last_error", "aapdhg_destroy", "aapdhg_batch_last_error",
-             "aapdhg_batch_destroy")
+             "aapdhg_batch_destroy", "aapdhg_server_last_error", "aapdhg_server_destroy")
 
 
 class AAPDHGError(RuntimeError):
@@ -87,7 +93,23 @@ def load(path: str = LIB_PATH):
     L.aapdhg_last_error.restype = C.c_char_p
     L.aapdhg_destroy.argtypes = [vp]
     L.aapdhg_destroy.restype = None
+    L.aapdhg_autotune.argtypes = [vp, vp, vp, vp]
+    L.aapdhg_set_task_shape.argtypes = [vp, i32, i32]
+    L.aapdhg_batch_autotune.argtypes = [vp, vp, vp, vp]
+    L.aapdhg_batch_set_task_shape.argtypes = [vp, i32, i32]
     L.aapdhg_batch_create.argtypes = [i32] + [vp] * 11 + [i32, vp, C.POINTER(vp)]
+    L.aapdhg_batch_set_tolerances.argtypes = [vp, vp]
+    L.aapdhg_batch_launch.argtypes = [vp, i64, f64, i32]
+    L.aapdhg_batch_poll.argtypes = [vp, vp]
+    L.aapdhg_server_create.argtypes = [i32, i32, i32, i32, i64, i64, C.POINTER(vp)]
+    L.aapdhg_server_submit.argtypes = [vp, i32, i32, i64] + [vp] * 8 + [f64, C.POINTER(i64)]
+    L.aapdhg_server_step.argtypes = [vp, vp, vp]
+    L.aapdhg_server_result.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
+    L.aapdhg_server_device_bytes.argtypes = [vp, C.POINTER(i64)]
+    L.aapdhg_server_last_error.argtypes = [vp]
+    L.aapdhg_server_last_error.restype = C.c_char_p
+    L.aapdhg_server_destroy.argtypes = [vp]
+    L.aapdhg_server_destroy.restype = None
     L.aapdhg_batch_set_steps.argtypes = [vp, vp, vp]
     L.aapdhg_batch_estimate_norms.argtypes = [vp, i32, C.c_uint64, vp]
     L.aapdhg_batch_set_method.argtypes = [vp, i32, i32, f64, f64, f64, f64, f64, f64, f64, i32,
@@ -282,6 +304,19 @@ class Solver:
         k = n.value
         return dict(branch=br[:k], gnorm=gn[:k], kkt=kk[:k], mk=mk[:k])
 
+    def autotune(self):
+        """Time every task shape of the two half-step kernels now; returns the
+        chosen shapes and the average launch time (us) of each shape."""
+        sx, sy = C.c_int32(), C.c_int32()
+        us = np.zeros(2 * TASK_SHAPES)
+        self._check(self._L.aapdhg_autotune(self._h, C.byref(sx), C.byref(sy), _ptr(us)))
+        return dict(shape_x=sx.value, shape_y=sy.value, x_us=us[:TASK_SHAPES].tolist(),
+                    y_us=us[TASK_SHAPES:].tolist())
+
+    def set_task_shape(self, shape_x, shape_y):
+        """Fix the half-step task shapes ((-1, -1): tune again at the next iterate)."""
+        self._check(self._L.aapdhg_set_task_shape(self._h, int(shape_x), int(shape_y)))
+
     KERNEL_KINDS = ("xstep", "ystep", "memory", "mix")
 
     def profile_kernels(self, enable=True):
@@ -317,6 +352,16 @@ class BatchSolver:
     """
 
     KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "kkt")
+
+    def autotune(self):
+        sx, sy = C.c_int32(), C.c_int32()
+        us = np.zeros(2 * TASK_SHAPES)
+        self._check(self._L.aapdhg_batch_autotune(self._h, C.byref(sx), C.byref(sy), _ptr(us)))
+        return dict(shape_x=sx.value, shape_y=sy.value, x_us=us[:TASK_SHAPES].tolist(),
+                    y_us=us[TASK_SHAPES:].tolist())
+
+    def set_task_shape(self, shape_x, shape_y):
+        self._check(self._L.aapdhg_batch_set_task_shape(self._h, int(shape_x), int(shape_y)))
 
     def __init__(self, problems, precision: str = "mixed", stream=None, torch_memory: bool = True):
         import torch
@@ -402,6 +447,22 @@ class BatchSolver:
     def reset(self):
         self._check(self._L.aapdhg_batch_reset(self._h))
 
+    def set_tolerances(self, tol):
+        """Per-problem tolerances (None: one tolerance, the iterate argument, for all)."""
+        t = None if tol is None else _f64(np.broadcast_to(np.asarray(tol, np.float64),
+                                                          (self.nprob,)), self.nprob)
+        self._check(self._L.aapdhg_batch_set_tolerances(self._h, _ptr(t)))
+
+    def launch(self, n_iters, tol=0.0, kkt_every=0):
+        """Enqueue n_iters batch iterations without waiting."""
+        self._check(self._L.aapdhg_batch_launch(self._h, int(n_iters), float(tol), int(kkt_every)))
+
+    def poll(self):
+        """Wait for the enqueued work; True when every problem has stopped."""
+        v = C.c_int32()
+        self._check(self._L.aapdhg_batch_poll(self._h, C.byref(v)))
+        return bool(v.value)
+
     def iterate(self, max_iters, tol=0.0, kkt_every=0):
         """Returns (all converged, batch iterations run)."""
         done = C.c_int64()
@@ -451,4 +512,84 @@ class BatchSolver:
     def device_bytes(self):
         b = C.c_int64()
         self._check(self._L.aapdhg_batch_device_bytes(self._h, C.byref(b)))
+        return b.value
+
+
+REQ_WAITING, REQ_RUNNING, REQ_CONVERGED, REQ_CAPPED, REQ_ERROR, REQ_REJECTED = range(6)
+REQ_NAMES = ("waiting", "running", "converged", "capped", "error", "rejected")
+
+
+class Server:
+    """A served stream of LPs with continuous batching (the server C ABI)."""
+
+    def __init__(self, method="aa", mem=10, max_cohorts=4, max_cohort_size=64, max_iters=100000,
+                 mem_budget=0, torch_memory=True):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the server has no CPU path")
+        L = load()
+        if torch_memory:
+            use_torch_allocator()
+        self._L = L
+        self._h = C.c_void_p()
+        m = METHODS[method] if isinstance(method, str) else int(method)
+        s = L.aapdhg_server_create(m, int(mem), int(max_cohorts), int(max_cohort_size),
+                                   int(max_iters), int(mem_budget), C.byref(self._h))
+        if s != OK:
+            raise AAPDHGError(s, L.aapdhg_server_last_error(None).decode())
+        self._size = {}
+
+    def _check(self, s):
+        if s != OK:
+            raise AAPDHGError(s, self._L.aapdhg_server_last_error(self._h).decode())
+
+    def close(self):
+        if self._h:
+            self._L.aapdhg_server_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, P, tol):
+        rp = np.ascontiguousarray(P.row_ptr, dtype=np.int64)
+        arrs = (rp, np.ascontiguousarray(P.col_idx, dtype=np.int32),
+                np.ascontiguousarray(P.val, dtype=np.float64),
+                np.ascontiguousarray(P.sense, dtype=np.int8), _f64(P.q, P.m), _f64(P.c, P.n),
+                _f64(P.l, P.n), _f64(P.u, P.n))
+        rid = C.c_int64()
+        self._check(self._L.aapdhg_server_submit(self._h, int(P.m), int(P.n), int(rp[-1]),
+                                                 *[_ptr(a) for a in arrs], float(tol),
+                                                 C.byref(rid)))
+        self._size[rid.value] = (int(P.m), int(P.n))
+        return rid.value
+
+    def step(self):
+        """One scheduling round; returns (cohorts running, LPs waiting)."""
+        r, w = C.c_int32(), C.c_int32()
+        self._check(self._L.aapdhg_server_step(self._h, C.byref(r), C.byref(w)))
+        return r.value, w.value
+
+    def result(self, rid):
+        m, n = self._size[rid]
+        st, it = C.c_int32(), C.c_int64(-1)
+        x, y, kkt, t3 = np.full(n, np.nan), np.full(m, np.nan), np.full(6, np.nan), np.zeros(3)
+        self._check(self._L.aapdhg_server_result(self._h, int(rid), C.byref(st), _ptr(x), _ptr(y),
+                                                 _ptr(kkt), C.byref(it), _ptr(t3)))
+        return dict(state=REQ_NAMES[st.value], x=x, y=y,
+                    kkt=dict(zip(("r_p", "r_d", "r_g", "kkt", "pobj", "dobj"), kkt.tolist())),
+                    iters=it.value, t_submit=t3[0], t_admit=t3[1], t_done=t3[2])
+
+    def device_bytes(self):
+        b = C.c_int64()
+        self._check(self._L.aapdhg_server_device_bytes(self._h, C.byref(b)))
         return b.value

@@ -28,7 +28,7 @@ def stale() -> bool:
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
-UNITS = ("aapdhg.cu", "batch.cu", "kkt_noalloc.cu")
+UNITS = ("aapdhg.cu", "batch.cu", "serve.cu", "kkt_noalloc.cu")
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

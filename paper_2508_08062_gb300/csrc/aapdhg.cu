@@ -33,6 +33,7 @@ void *g_ctx = nullptr;
 thread_local std::string g_create_err;
 
 constexpr int CHUNK_ITERS = 64;   // iterations launched between two host polls
+static_assert(NSHAPE == AAPDHG_TASK_SHAPES, "task shapes of the C ABI and the kernels differ");
 
 }  // namespace
 
@@ -240,6 +241,11 @@ struct aapdhg_s {
     };
     std::vector<GraphEntry> graphs;
     bool use_graphs = true;
+    // task shapes of the two half-step kernels (autotuned at the first iterate)
+    int32_t shape_x = 0, shape_y = 0;
+    bool tuned = false, autotune = true;
+    int32_t gridx[NSHAPE] = {1, 1, 1}, gridy[NSHAPE] = {1, 1, 1};
+    double tune_us[2 * NSHAPE] = {0, 0, 0, 0, 0, 0};
     int32_t dhat_mode = -1;                // mode D-hat was last formed with
     bool scaled = false;                   // aapdhg_set_scaling applied
     std::vector<double> dr_host, dc_host;  // Dr, Dc in internal order (when scaled)
@@ -314,6 +320,15 @@ __global__ void __launch_bounds__(BLOCK) k_norm2(const V *v, int64_t len, double
         const double s = block_sum_partials(part, gridDim.x, 1, 0, sh);
         if (threadIdx.x == 0) st->scratch[slot] = s;
     }
+}
+
+template <class K> int occupancy(K kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BLOCK, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return std::max(occ, 1);
 }
 
 template <typename V> Prob<V> &prob(aapdhg_t h);
@@ -404,21 +419,30 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     if (!P.UP || !P.dh || !P.g) ok = false;
     h->d_UP = P.UP;
 
-    // fixed grids (deterministic reductions)
-    int occ1 = 0, occ2 = 0, occ3 = 0;
-    // grids sized for the common (non-KKT) variants, all of whose blocks are
-    // resident; a KKT launch (one in kkt_every) may run a short second wave
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep<V, false>, BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep<V, false>, BLOCK, 0);
+    // fixed grids per task shape (deterministic reductions), sized for the
+    // common (non-KKT) variants, all of whose blocks are resident; a KKT
+    // launch (one in kkt_every) may run a short second wave
+    int occ3 = 0;
+    const int occx[NSHAPE] = {occupancy(k_xstep<V, false, 0>), occupancy(k_xstep<V, false, 1>),
+                              occupancy(k_xstep<V, false, 2>)};
+    const int occy[NSHAPE] = {occupancy(k_ystep<V, false, 0>), occupancy(k_ystep<V, false, 1>),
+                              occupancy(k_ystep<V, false, 2>)};
+    int gmax1 = 1, gmax2 = 1;
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        const int g = task_shape(sh).g;
+        h->gridx[sh] = grid_for(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
+        h->gridy[sh] = grid_for(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
+        gmax1 = std::max(gmax1, h->gridx[sh]);
+        gmax2 = std::max(gmax2, h->gridy[sh]);
+    }
+    P.grid1 = h->gridx[0];
+    P.grid2 = h->gridy[0];
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, 20>, BLOCK, 0);
-    const int64_t tasksT = P.KT.ntasks(), tasksK = P.K.ntasks();
-    P.grid1 = grid_for(h, (tasksT + WARPS - 1) / WARPS, occ1);
-    P.grid2 = grid_for(h, (tasksK + WARPS - 1) / WARPS, occ2);
 
     P.grid3 = grid_for(h, (N + BLOCK - 1) / BLOCK, std::max(occ3, 1));
     h->grid5 = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
-    P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * P.grid1);
-    P.part2 = (double *)dev_alloc(h, sizeof(double) * 3 * P.grid2);
+    P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * gmax1);
+    P.part2 = (double *)dev_alloc(h, sizeof(double) * 3 * gmax2);
     P.part3 = (double *)dev_alloc(h, sizeof(double) * (MAXM + 3) * h->sm_count * 8);
     h->st = (DevState *)dev_alloc(h, sizeof(DevState));
     P.st = h->st;
@@ -516,16 +540,79 @@ template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode) {
     }
 }
 
-template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
+template <typename V, bool KKT> void launch_x(aapdhg_t h, int shape, int mode) {
     Prob<V> &P = prob<V>(h);
+    if (shape == 1) k_xstep<V, KKT, 1><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 2) k_xstep<V, KKT, 2><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else k_xstep<V, KKT, 0><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+}
+
+template <typename V, bool KKT> void launch_y(aapdhg_t h, int shape, int mode) {
+    Prob<V> &P = prob<V>(h);
+    if (shape == 1) k_ystep<V, KKT, 1><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 2) k_ystep<V, KKT, 2><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else k_ystep<V, KKT, 0><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+}
+
+template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
     mark_begin(h, KIND_XSTEP);
-    if (kkt) k_xstep<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-    else k_xstep<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    if (kkt) launch_x<V, true>(h, h->shape_x, mode);
+    else launch_x<V, false>(h, h->shape_x, mode);
     mark_end(h);
     mark_begin(h, KIND_YSTEP);
-    if (kkt) k_ystep<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
-    else k_ystep<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    if (kkt) launch_y<V, true>(h, h->shape_y, mode);
+    else launch_y<V, false>(h, h->shape_y, mode);
     mark_end(h);
+}
+
+void set_shapes(aapdhg_t h, int sx, int sy) {
+    h->shape_x = sx;
+    h->shape_y = sy;
+    h->pf.grid1 = h->pd.grid1 = h->gridx[sx];
+    h->pf.grid2 = h->pd.grid2 = h->gridy[sy];
+}
+
+void drop_graphs(aapdhg_t h);
+
+// Autotuning of the two half-step kernels: every compiled task shape is
+// launched on the handle's matrices (timing mode: T(u) goes to the scratch
+// component, no run state changes), twice to warm up and five times under
+// CUDA events; the fastest shape of each kernel is kept.
+template <typename V> aapdhg_status autotune_t(aapdhg_t h) {
+    Prob<V> &P = prob<V>(h);
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    float best_x = 1e30f, best_y = 1e30f;
+    int bx = 0, by = 0;
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        P.grid1 = h->gridx[sh];
+        P.grid2 = h->gridy[sh];
+        for (int w = 0; w < 2; ++w) launch_x<V, false>(h, sh, MODE_TUNE);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 5; ++r) launch_x<V, false>(h, sh, MODE_TUNE);
+        cudaEventRecord(e1, h->stream);
+        CK(h, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->tune_us[sh] = 1e3 * ms / 5;
+        if (ms < best_x) { best_x = ms; bx = sh; }
+        for (int w = 0; w < 2; ++w) launch_y<V, false>(h, sh, MODE_TUNE);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 5; ++r) launch_y<V, false>(h, sh, MODE_TUNE);
+        cudaEventRecord(e1, h->stream);
+        CK(h, cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->tune_us[NSHAPE + sh] = 1e3 * ms / 5;
+        if (ms < best_y) { best_y = ms; by = sh; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(h, cudaGetLastError());
+    set_shapes(h, bx, by);
+    h->tuned = true;
+    drop_graphs(h);
+    return AAPDHG_OK;
 }
 
 template <typename V> void launch_memory_any(aapdhg_t h, int mode) {
@@ -609,6 +696,7 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
     h->mp.kkt_every = kkt_every;
     aapdhg_status s = ensure_rings<V>(h, (h->mp.method == 0) ? 0 : h->mp.mem);
     if (s != AAPDHG_OK) return s;
+    if (h->autotune && !h->tuned && (s = autotune_t<V>(h)) != AAPDHG_OK) return s;
     if ((s = read_state(h)) != AAPDHG_OK) return s;
     if (!h->st_host->init_done) {
         launch_iteration<V>(h, false, MODE_INIT);
@@ -1056,6 +1144,33 @@ aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launc
         if (launches) *launches = h->prof_n[kind];
         if (total_ms) *total_ms = h->prof_ms[kind];
     }
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? autotune_t<double>(h) : autotune_t<float>(h);
+    if (s != AAPDHG_OK) return s;
+    if (shape_x) *shape_x = h->shape_x;
+    if (shape_y) *shape_y = h->shape_y;
+    if (avg_us) for (int k = 0; k < 2 * NSHAPE; ++k) avg_us[k] = h->tune_us[k];
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (shape_x == -1 && shape_y == -1) {
+        h->autotune = true;
+        h->tuned = false;
+        return AAPDHG_OK;
+    }
+    if (shape_x < 0 || shape_x >= NSHAPE || shape_y < 0 || shape_y >= NSHAPE)
+        return fail(h, AAPDHG_ERR_INVALID, "task shapes are 0 .. AAPDHG_TASK_SHAPES - 1, or both -1");
+    h->autotune = false;
+    set_shapes(h, shape_x, shape_y);
+    drop_graphs(h);
     return AAPDHG_OK;
 }
 

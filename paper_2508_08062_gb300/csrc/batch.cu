@@ -68,6 +68,7 @@ struct aapdhg_batch_s {
     BatchView<double> bd{};
     MethodParams mp{};
     DevState *stb = nullptr;
+    double *ptol_dev = nullptr;                    // per-problem tolerances (when set)
     unsigned char *hdr_host = nullptr;             // pinned: nprob headers
     int64_t g = 0;                                 // batch iterations launched (the start one included)
     int32_t kkt_every = 0;
@@ -80,6 +81,11 @@ struct aapdhg_batch_s {
     struct GraphEntry { cudaGraphExec_t exec; int64_t phase; int parity; int32_t kkt_every; double tol; };
     std::vector<GraphEntry> graphs;
     bool use_graphs = true;
+    // task shapes of the two half-step kernels (autotuned at the first iterate)
+    int32_t shape_x = 0, shape_y = 0;
+    bool tuned = false, autotune = true;
+    int32_t gridx[NSHAPE] = {1, 1, 1}, gridy[NSHAPE] = {1, 1, 1};
+    double tune_us[2 * NSHAPE] = {0, 0, 0, 0, 0, 0};
     // instrumentation
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;
@@ -142,6 +148,15 @@ template <> BatchView<double> &bview<double>(bh_t h) { return h->bd; }
 int bgrid(bh_t h, int64_t need, int occ) {
     const int64_t cap = (int64_t)h->sm_count * std::max(occ, 1);
     return (int)std::max<int64_t>(1, std::min<int64_t>(need, cap));
+}
+
+template <class K> int boccupancy(K kernel) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, BLOCK, 0) != cudaSuccess) {
+        cudaGetLastError();
+        occ = 1;
+    }
+    return std::max(occ, 1);
 }
 
 void bmark_begin(bh_t h, int kind) {
@@ -220,12 +235,18 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     P.tr = Trace{0, nullptr, nullptr, nullptr, nullptr};
     P.st = nullptr;
     if (!P.UP || !P.dh || !P.g) ok = false;
-    int occ1 = 0, occ2 = 0;
-    // grids for the common (non-KKT) variants: all their blocks resident
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, k_xstep_b<V, false>, BLOCK, 0);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, k_ystep_b<V, false>, BLOCK, 0);
-    P.grid1 = bgrid(h, (P.KT.ntasks() + WARPS - 1) / WARPS, occ1);
-    P.grid2 = bgrid(h, (P.K.ntasks() + WARPS - 1) / WARPS, occ2);
+    // grids per task shape for the common (non-KKT) variants: all their blocks resident
+    const int occx[NSHAPE] = {boccupancy(k_xstep_b<V, false, 0>), boccupancy(k_xstep_b<V, false, 1>),
+                              boccupancy(k_xstep_b<V, false, 2>)};
+    const int occy[NSHAPE] = {boccupancy(k_ystep_b<V, false, 0>), boccupancy(k_ystep_b<V, false, 1>),
+                              boccupancy(k_ystep_b<V, false, 2>)};
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        const int g = task_shape(sh).g;
+        h->gridx[sh] = bgrid(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
+        h->gridy[sh] = bgrid(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
+    }
+    P.grid1 = h->gridx[0];
+    P.grid2 = h->gridy[0];
 
     // chunks of every problem's elements: its variables, then its constraints
     std::vector<int4> chunk;
@@ -324,22 +345,84 @@ template <typename V, int MC> void blaunch_memory_mix(bh_t h, int cur) {
     }
 }
 
-template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
+template <typename V, bool KKT> void blaunch_x(bh_t h, int shape, int cur, int mode) {
     Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    if (shape == 1) k_xstep_b<V, KKT, 1><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 2) k_xstep_b<V, KKT, 2><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else k_xstep_b<V, KKT, 0><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+}
+
+template <typename V, bool KKT> void blaunch_y(bh_t h, int shape, int cur, int mode) {
+    Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    if (shape == 1) k_ystep_b<V, KKT, 1><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 2) k_ystep_b<V, KKT, 2><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else k_ystep_b<V, KKT, 0><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+}
+
+void bset_shapes(bh_t h, int sx, int sy) {
+    h->shape_x = sx;
+    h->shape_y = sy;
+    h->pf.grid1 = h->pd.grid1 = h->gridx[sx];
+    h->pf.grid2 = h->pd.grid2 = h->gridy[sy];
+}
+
+// Autotuning of the two half-step kernels, as for the single-LP solver: every
+// task shape timed on the packed matrices (timing mode: no run state changes).
+template <typename V> aapdhg_status bautotune(bh_t h) {
+    Prob<V> &P = bprob<V>(h);
+    const int cur = (int)(h->g & 1);
+    cudaEvent_t e0, e1;
+    BCK(h, cudaEventCreate(&e0));
+    BCK(h, cudaEventCreate(&e1));
+    float best_x = 1e30f, best_y = 1e30f;
+    int bx = 0, by = 0;
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        P.grid1 = h->gridx[sh];
+        P.grid2 = h->gridy[sh];
+        float ms = 0.f;
+        for (int w = 0; w < 2; ++w) blaunch_x<V, false>(h, sh, cur, MODE_TUNE);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 5; ++r) blaunch_x<V, false>(h, sh, cur, MODE_TUNE);
+        cudaEventRecord(e1, h->stream);
+        BCK(h, cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->tune_us[sh] = 1e3 * ms / 5;
+        if (ms < best_x) { best_x = ms; bx = sh; }
+        for (int w = 0; w < 2; ++w) blaunch_y<V, false>(h, sh, cur, MODE_TUNE);
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 5; ++r) blaunch_y<V, false>(h, sh, cur, MODE_TUNE);
+        cudaEventRecord(e1, h->stream);
+        BCK(h, cudaEventSynchronize(e1));
+        cudaEventElapsedTime(&ms, e0, e1);
+        h->tune_us[NSHAPE + sh] = 1e3 * ms / 5;
+        if (ms < best_y) { best_y = ms; by = sh; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    BCK(h, cudaGetLastError());
+    bset_shapes(h, bx, by);
+    h->tuned = true;
+    bdrop_graphs(h);
+    return AAPDHG_OK;
+}
+
+template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
     BatchView<V> &B = bview<V>(h);
     const int cur = (int)(g & 1);
     const bool kkt = mode == MODE_EVAL || (h->kkt_every > 0 && g >= 1 && (g - 1) % h->kkt_every == 0);
     bmark_begin(h, BK_XSTEP);
-    if (kkt) k_xstep_b<V, true><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
-    else k_xstep_b<V, false><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    if (kkt) blaunch_x<V, true>(h, h->shape_x, cur, mode);
+    else blaunch_x<V, false>(h, h->shape_x, cur, mode);
     bmark_end(h);
     bmark_begin(h, BK_YSTEP);
-    if (kkt) k_ystep_b<V, true><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
-    else k_ystep_b<V, false><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    if (kkt) blaunch_y<V, true>(h, h->shape_y, cur, mode);
+    else blaunch_y<V, false>(h, h->shape_y, cur, mode);
     bmark_end(h);
     if (kkt) {
         bmark_begin(h, BK_KKT);
-        k_kkt_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(B, h->mp.tol, mode);
+        k_kkt_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(B, h->mp.tol, mode);   // ptol overrides tol
         bmark_end(h);
     }
     if (mode == MODE_EVAL) return;
@@ -411,12 +494,15 @@ aapdhg_status bread_headers(bh_t h) {
 
 const DevState *hdr(bh_t h, int32_t p) { return reinterpret_cast<const DevState *>(h->hdr_host + HDR * p); }
 
-template <typename V> aapdhg_status biterate(bh_t h, int64_t max_iters, double tol, int32_t kkt_every,
-                                            int64_t *iters_done) {
+// Start of a solve call: rings, autotuning, then u^1 = T u^0 of every problem
+// (first call) or a re-test of converged problems (later calls).  Enqueues
+// work only.
+template <typename V> aapdhg_status bbegin(bh_t h, double tol, int32_t kkt_every) {
     h->mp.tol = tol;
     h->kkt_every = kkt_every;
     aapdhg_status s = AAPDHG_OK;
     if (h->mp.method != 0 && h->mp.mem > 0 && (s = bensure_rings<V>(h)) != AAPDHG_OK) return s;
+    if (h->autotune && !h->tuned && (s = bautotune<V>(h)) != AAPDHG_OK) return s;
     if (h->g == 0) {
         blaunch_iteration<V>(h, 0, MODE_ITER);   // u^1 = T u^0 and g^0 of every problem
         h->g = 1;
@@ -425,25 +511,25 @@ template <typename V> aapdhg_status biterate(bh_t h, int64_t max_iters, double t
         h->launches += 1;
     }
     BCK(h, cudaGetLastError());
-    if ((s = bread_headers(h)) != AAPDHG_OK) return s;
-    auto all_stopped = [&]() {
-        for (int32_t p = 0; p < h->nprob; ++p)
-            if (!hdr(h, p)->done && !hdr(h, p)->error) return false;
-        return true;
-    };
-    int64_t launched = 0;
-    bool stop = all_stopped();
-    while (launched < max_iters && !stop) {
-        const int64_t chunk = std::min<int64_t>(B_CHUNK_ITERS, max_iters - launched);
-        if (!(chunk == B_CHUNK_ITERS && blaunch_chunk_graph<V>(h, h->g)))
-            for (int64_t c = 0; c < chunk; ++c) blaunch_iteration<V>(h, h->g + c, MODE_ITER);
-        BCK(h, cudaGetLastError());
-        h->g += chunk;
-        launched += chunk;
-        if ((s = bread_headers(h)) != AAPDHG_OK) return s;
-        stop = all_stopped();
-    }
-    if (iters_done) *iters_done = launched;
+    return AAPDHG_OK;
+}
+
+// Enqueue n batch iterations (a CUDA graph when n is a full chunk).
+template <typename V> aapdhg_status blaunch_chunk(bh_t h, int64_t n) {
+    if (!(n == B_CHUNK_ITERS && blaunch_chunk_graph<V>(h, h->g)))
+        for (int64_t c = 0; c < n; ++c) blaunch_iteration<V>(h, h->g + c, MODE_ITER);
+    BCK(h, cudaGetLastError());
+    h->g += n;
+    return AAPDHG_OK;
+}
+
+bool ball_stopped(bh_t h) {
+    for (int32_t p = 0; p < h->nprob; ++p)
+        if (!hdr(h, p)->done && !hdr(h, p)->error) return false;
+    return true;
+}
+
+aapdhg_status bfinal_status(bh_t h) {
     bool any_err = false, all_done = true;
     for (int32_t p = 0; p < h->nprob; ++p) {
         any_err |= hdr(h, p)->error != 0;
@@ -454,6 +540,24 @@ template <typename V> aapdhg_status biterate(bh_t h, int64_t max_iters, double t
         return AAPDHG_ERR_NUMERIC;
     }
     return all_done ? AAPDHG_OK : AAPDHG_NOT_CONVERGED;
+}
+
+template <typename V> aapdhg_status biterate(bh_t h, int64_t max_iters, double tol, int32_t kkt_every,
+                                            int64_t *iters_done) {
+    aapdhg_status s = bbegin<V>(h, tol, kkt_every);
+    if (s != AAPDHG_OK) return s;
+    if ((s = bread_headers(h)) != AAPDHG_OK) return s;
+    int64_t launched = 0;
+    bool stop = ball_stopped(h);
+    while (launched < max_iters && !stop) {
+        const int64_t chunk = std::min<int64_t>(B_CHUNK_ITERS, max_iters - launched);
+        if ((s = blaunch_chunk<V>(h, chunk)) != AAPDHG_OK) return s;
+        launched += chunk;
+        if ((s = bread_headers(h)) != AAPDHG_OK) return s;
+        stop = ball_stopped(h);
+    }
+    if (iters_done) *iters_done = launched;
+    return bfinal_status(h);
 }
 
 template <typename V> aapdhg_status bget_iterate(bh_t h, double *x, double *y) {
@@ -841,6 +945,28 @@ aapdhg_status aapdhg_batch_reset(aapdhg_batch_t h) {
     return breset_any(h);
 }
 
+aapdhg_status aapdhg_batch_set_tolerances(aapdhg_batch_t h, const double *tol) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!tol) {
+        h->bd.ptol = h->bf.ptol = nullptr;
+        bdrop_graphs(h);
+        return AAPDHG_OK;
+    }
+    for (int32_t p = 0; p < h->nprob; ++p)
+        if (!(tol[p] >= 0)) return bfail(h, AAPDHG_ERR_INVALID, "tolerances must be >= 0");
+    if (!h->ptol_dev) {
+        h->ptol_dev = (double *)bdev_alloc(h, sizeof(double) * h->nprob);
+        if (!h->ptol_dev) return bfail(h, AAPDHG_ERR_OOM, "tolerance array");
+    }
+    BCK(h, cudaMemcpyAsync(h->ptol_dev, tol, sizeof(double) * h->nprob, cudaMemcpyHostToDevice, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    if (h->prec == AAPDHG_FP64) h->bd.ptol = h->ptol_dev;
+    else h->bf.ptol = h->ptol_dev;
+    bdrop_graphs(h);
+    return AAPDHG_OK;
+}
+
 aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double tol, int32_t kkt_every,
                                    int64_t *iters_done) {
     if (!h) return AAPDHG_ERR_INVALID;
@@ -851,6 +977,37 @@ aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double t
         if (!(h->tau[p] > 0)) return bfail(h, AAPDHG_ERR_INVALID, "set_steps must be called before iterate");
     return h->prec == AAPDHG_FP64 ? biterate<double>(h, max_iters, tol, kkt_every, iters_done)
                                   : biterate<float>(h, max_iters, tol, kkt_every, iters_done);
+}
+
+aapdhg_status aapdhg_batch_launch(aapdhg_batch_t h, int64_t n_iters, double tol, int32_t kkt_every) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (n_iters < 0 || kkt_every < 0 || !(tol >= 0))
+        return bfail(h, AAPDHG_ERR_INVALID, "need n_iters >= 0, kkt_every >= 0, tol >= 0");
+    for (int32_t p = 0; p < h->nprob; ++p)
+        if (!(h->tau[p] > 0)) return bfail(h, AAPDHG_ERR_INVALID, "set_steps must be called before launch");
+    const bool fp64 = h->prec == AAPDHG_FP64;
+    aapdhg_status s = AAPDHG_OK;
+    if (h->g == 0) {
+        s = fp64 ? bbegin<double>(h, tol, kkt_every) : bbegin<float>(h, tol, kkt_every);
+    } else {
+        h->mp.tol = tol;
+        h->kkt_every = kkt_every;
+    }
+    for (int64_t done = 0; s == AAPDHG_OK && done < n_iters; done += B_CHUNK_ITERS) {
+        const int64_t n = std::min<int64_t>(B_CHUNK_ITERS, n_iters - done);
+        s = fp64 ? blaunch_chunk<double>(h, n) : blaunch_chunk<float>(h, n);
+    }
+    return s;
+}
+
+aapdhg_status aapdhg_batch_poll(aapdhg_batch_t h, int32_t *all_stopped) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    aapdhg_status s = bread_headers(h);
+    if (s != AAPDHG_OK) return s;
+    if (all_stopped) *all_stopped = ball_stopped(h) ? 1 : 0;
+    return AAPDHG_OK;
 }
 
 aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y) {
@@ -905,6 +1062,33 @@ aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, in
     if (kind < 0 || kind >= BK_N) return bfail(h, AAPDHG_ERR_INVALID, "unknown kernel kind");
     *launches = h->prof_n[kind];
     *total_ms = h->prof_ms[kind];
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_autotune(aapdhg_batch_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? bautotune<double>(h) : bautotune<float>(h);
+    if (s != AAPDHG_OK) return s;
+    if (shape_x) *shape_x = h->shape_x;
+    if (shape_y) *shape_y = h->shape_y;
+    if (avg_us) for (int k = 0; k < 2 * NSHAPE; ++k) avg_us[k] = h->tune_us[k];
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_set_task_shape(aapdhg_batch_t h, int32_t shape_x, int32_t shape_y) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (shape_x == -1 && shape_y == -1) {
+        h->autotune = true;
+        h->tuned = false;
+        return AAPDHG_OK;
+    }
+    if (shape_x < 0 || shape_x >= NSHAPE || shape_y < 0 || shape_y >= NSHAPE)
+        return bfail(h, AAPDHG_ERR_INVALID, "task shapes are 0 .. AAPDHG_TASK_SHAPES - 1, or both -1");
+    h->autotune = false;
+    bset_shapes(h, shape_x, shape_y);
+    bdrop_graphs(h);
     return AAPDHG_OK;
 }
 

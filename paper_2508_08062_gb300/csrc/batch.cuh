@@ -51,6 +51,7 @@ template <typename V> struct BatchView {
     double *cpart;                    // nchunk * NBV chunk partials
     uint32_t *pcnt;                   // per-problem arrival counters (self-resetting)
     const double *pnorm;              // per problem: ||q||, ||c|| of the caller's LP
+    const double *ptol;               // per-problem tolerances, or null (one tolerance for all)
 };
 
 __device__ __forceinline__ bool stopped(const DevState *s) { return (s->done | s->error) != 0; }
@@ -137,27 +138,29 @@ template <typename V, bool KKT> struct EpiYB {
     }
 };
 
-template <typename V, bool KKT>
+template <typename V, bool KKT, int S = 0>
 __global__ void __launch_bounds__(BLOCK) k_xstep_b(Prob<V> P, BatchView<V> B, int cur, int mode) {
+    constexpr TaskShape ts = task_shape(S);
     GatherY<V> gat{reinterpret_cast<const V *>(P.UP + P.n) + cur};
     EpiXB<V, KKT> epi{P, B, cur, mode};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.KT.ntasks();
+    const int64_t ntask = P.KT.ntasks(ts.g);
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
-        if (t < ntask) run_task<V, 1>(P.KT, t, gat, epi);
+        if (t < ntask) run_task<V, 1, ts.g, ts.ld>(P.KT, t, gat, epi);
     }
 }
 
-template <typename V, bool KKT>
+template <typename V, bool KKT, int S = 0>
 __global__ void __launch_bounds__(BLOCK) k_ystep_b(Prob<V> P, BatchView<V> B, int cur, int mode) {
+    constexpr TaskShape ts = task_shape(S);
     GatherXZ<V, KKT> gat{P.UP, cur};
     EpiYB<V, KKT> epi{P, B, cur, mode};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.K.ntasks();
+    const int64_t ntask = P.K.ntasks(ts.g);
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
-        if (t < ntask) run_task<V, KKT ? 2 : 1>(P.K, t, gat, epi);
+        if (t < ntask) run_task<V, KKT ? 2 : 1, ts.g, ts.ld>(P.K, t, gat, epi);
     }
 }
 
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(BLOCK) k_kkt_b(BatchView<V> B, double tol, int
     st->kkt_valid = 1;
     if (mode == MODE_ITER) {
         if (!isfinite(out[3])) st->error = 1;
-        else if (out[3] <= tol) st->done = 1;
+        else if (out[3] <= (B.ptol ? B.ptol[p] : tol)) st->done = 1;
     }
 }
 

@@ -14,6 +14,19 @@ constexpr int SELL_MAX = 32;        // rows up to this length go to SELL-32 slic
 constexpr int LOADS = 8;            // independent loads a lane keeps in flight
 constexpr int SLICES_PER_TASK = 2;  // SELL slices one warp reads in lockstep
 
+// Task shapes the SpMV kernels are compiled for: SELL slices per warp task and
+// loads a lane keeps in flight.  The runtimes time every shape of the two
+// half-step kernels on the actual matrices and keep the fastest (autotuning).
+// All shapes sum every row in the same order, so the choice never changes a
+// result.  Shape 0 is the default.
+struct TaskShape {
+    int g, ld;
+};
+constexpr int NSHAPE = 3;
+__host__ __device__ constexpr TaskShape task_shape(int s) {
+    return s == 1 ? TaskShape{1, 8} : (s == 2 ? TaskShape{4, 8} : TaskShape{SLICES_PER_TASK, LOADS});
+}
+
 // ---------------------------------------------------------------------------
 // Accumulators.  FP64 mode: plain double.  Mixed mode: a float pair (hi, lo)
 // fed with error-free transformations (exact product via fma, TwoSum), so a
@@ -152,8 +165,8 @@ template <typename V> struct CSRView {
     const V *sell_val;
     V *chunk_part;                // n_chunks * 2 partial sums of split rows
     uint32_t *chunk_cnt;          // arrival counters by long-row id (self-resetting)
-    __host__ __device__ int64_t ntasks() const {
-        return (int64_t)n_chunks + (n_slices + SLICES_PER_TASK - 1) / SLICES_PER_TASK;
+    __host__ __device__ int64_t ntasks(int g = SLICES_PER_TASK) const {
+        return (int64_t)n_chunks + (n_slices + g - 1) / g;
     }
 };
 
@@ -211,9 +224,10 @@ __device__ __forceinline__ Pack<V, W> ld_stream(const V *p) {
 template <typename V, int W>
 __device__ __forceinline__ void st(V *p, const Pack<V, W> &v) { *reinterpret_cast<Pack<V, W> *>(p) = v; }
 
-// Kernel modes: forming u^1 = T u^0 and g^0, a loop iteration, or a KKT
-// evaluation of the current iterate that changes no run state.
-enum { MODE_INIT = 0, MODE_ITER = 1, MODE_EVAL = 2 };
+// Kernel modes: forming u^1 = T u^0 and g^0, a loop iteration, a KKT
+// evaluation of the current iterate that changes no run state, or a timing
+// launch of a half-step (autotuning) that changes no run state either.
+enum { MODE_INIT = 0, MODE_ITER = 1, MODE_EVAL = 2, MODE_TUNE = 3 };
 
 // Block-wide sum of NV per-thread accumulators into FP64 (fixed order),
 // written to out[0..NV) by thread 0 of the block.  `sh` holds WARPS * NV doubles.

@@ -35,7 +35,7 @@ namespace aap {
 // on), so a lane's row is known without the slice's metadata and its inputs
 // are requested together with that metadata; otherwise (a batch) the row
 // comes from the metadata.
-template <typename V, int NACC, class Gather, class Epi>
+template <typename V, int NACC, int G = SLICES_PER_TASK, int LD = LOADS, class Gather, class Epi>
 __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather &gather, Epi &epi) {
     typedef typename Epi::Pre Pre;
     const int lane = threadIdx.x & 31;
@@ -61,17 +61,17 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
         const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
         Pre pre;
         if (nch == 1 && lane == 0) pre = epi.pre(r, cm.z);
-        for (int kb = k0 + lane; kb < k1; kb += 32 * LOADS) {
-            int ci[LOADS];
-            V va[LOADS];
+        for (int kb = k0 + lane; kb < k1; kb += 32 * LD) {
+            int ci[LD];
+            V va[LD];
 #pragma unroll
-            for (int j = 0; j < LOADS; ++j) {
+            for (int j = 0; j < LD; ++j) {
                 const int k = kb + 32 * j;
                 ci[j] = k < k1 ? __ldcs(A.ci + k) : 0;
                 va[j] = k < k1 ? __ldcs(A.val + k) : V(0);
             }
 #pragma unroll
-            for (int j = 0; j < LOADS; ++j)
+            for (int j = 0; j < LD; ++j)
                 if (kb + 32 * j < k1) gather(ci[j], va[j], acc);
         }
 #pragma unroll
@@ -105,10 +105,9 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
         return;
     }
 
-    // SLICES_PER_TASK SELL-32 slices in lockstep: lane = row of each slice,
-    // entry tt of a slice's 32 rows contiguous; padding entries are zeros.
-    constexpr int G = SLICES_PER_TASK;
-    constexpr int B = LOADS / G;
+    // G SELL-32 slices in lockstep: lane = row of each slice, entry tt of a
+    // slice's 32 rows contiguous; padding entries are zeros.
+    constexpr int B = LD / G;
     const int sl0 = (int)(t - A.n_chunks) * G;
     int2 meta[G];
     int r[G];
@@ -224,19 +223,20 @@ template <typename V, bool KKT> struct EpiX {
     }
 };
 
-template <typename V, bool KKT>
+template <typename V, bool KKT, int S = 0>
 __global__ void __launch_bounds__(BLOCK) k_xstep(Prob<V> P, MethodParams mp, int mode) {
-    if (mode != MODE_EVAL && (P.st->done | P.st->error)) return;
+    constexpr TaskShape ts = task_shape(S);
+    if (mode < MODE_EVAL && (P.st->done | P.st->error)) return;
     const int cur = (mode == MODE_INIT || !P.st->init_done) ? 0 : (int)(P.st->it & 1) ^ 1;
     __shared__ double sh[WARPS * 4];
     Acc<V> g2, dres2, lam, cx;
     GatherY<V> gat{reinterpret_cast<const V *>(P.UP + P.n) + cur};
     EpiX<V, KKT> epi{P, (V)mp.tau, cur, g2, dres2, lam, cx};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.KT.ntasks();
+    const int64_t ntask = P.KT.ntasks(ts.g);
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
-        if (t < ntask) run_task<V, 1>(P.KT, t, gat, epi);
+        if (t < ntask) run_task<V, 1, ts.g, ts.ld>(P.KT, t, gat, epi);
     }
     Acc<V> a4[4] = {g2, dres2, lam, cx};
     block_reduce_store<V, 4>(a4, sh, P.part1 + (int64_t)blockIdx.x * 4);
@@ -335,20 +335,22 @@ __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, b
     st->want_aa = want ? 1 : 0;
 }
 
-template <typename V, bool KKT>
+template <typename V, bool KKT, int S = 0>
 __global__ void __launch_bounds__(BLOCK) k_ystep(Prob<V> P, MethodParams mp, int mode) {
-    if (mode != MODE_EVAL && (P.st->done | P.st->error)) return;
+    constexpr TaskShape ts = task_shape(S);
+    if (mode < MODE_EVAL && (P.st->done | P.st->error)) return;
     const int cur = (mode == MODE_INIT || !P.st->init_done) ? 0 : (int)(P.st->it & 1) ^ 1;
     __shared__ double sh[WARPS * 3];
     Acc<V> g2, pres2, qy;
     GatherXZ<V, KKT> gat{P.UP, cur};
     EpiY<V, KKT> epi{P, (V)mp.sigma, cur, g2, pres2, qy};
     const int warp = threadIdx.x >> 5;
-    const int64_t ntask = P.K.ntasks();
+    const int64_t ntask = P.K.ntasks(ts.g);
     for (int64_t vb = blockIdx.x; vb * WARPS < ntask; vb += gridDim.x) {
         const int64_t t = vb * WARPS + warp;
-        if (t < ntask) run_task<V, KKT ? 2 : 1>(P.K, t, gat, epi);
+        if (t < ntask) run_task<V, KKT ? 2 : 1, ts.g, ts.ld>(P.K, t, gat, epi);
     }
+    if (mode == MODE_TUNE) return;
     Acc<V> a3[3] = {g2, pres2, qy};
     block_reduce_store<V, 3>(a3, sh, P.part2 + (int64_t)blockIdx.x * 3);
     if (last_block(&P.st->cnt_spmv)) finalize_T<V>(P, mp, mode, KKT);

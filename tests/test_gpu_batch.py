@@ -321,3 +321,22 @@ def test_batch_rejects_an_invalid_member():
     with _batch([good, good]) as b:
         with pytest.raises(AAPDHGError):
             b.iterate(1)                     # no step sizes yet
+
+
+def test_batch_task_shapes_give_identical_iterates():
+    probs = _members()
+    taus = np.array([0.9 / _norm(P) for P in probs])
+    got = []
+    for shapes in ((0, 0), (1, 1), (2, 2), None):
+        with _batch(probs, "mixed") as b:
+            b.set_steps(taus, taus)
+            b.set_method("aa", mem=5)
+            if shapes is None:
+                t = b.autotune()
+                assert t["shape_x"] in (0, 1, 2) and t["shape_y"] in (0, 1, 2)
+            else:
+                b.set_task_shape(*shapes)
+            b.iterate(30)
+            got.append(np.concatenate([np.concatenate(xy) for xy in b.get_iterate()]))
+    for u in got[1:]:
+        assert np.array_equal(u, got[0])

@@ -294,3 +294,34 @@ def test_scaling_only_once_and_start_in_caller_units():
         assert np.allclose(x, x0, rtol=1e-14) and np.allclose(y, y0, rtol=1e-14)
         with pytest.raises(AAPDHGError):
             s.set_scaling(10, True)
+
+
+# --------------------------------------------------------------------------
+# Autotuning of the half-step task shapes: the shape never changes a result
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_task_shapes_give_identical_iterates(prec):
+    P = _with_long_row_and_column(3)
+    tau, sig = _steps(P)
+    got = []
+    for shapes in ((0, 0), (1, 1), (2, 2), (1, 2), None):
+        with _solver(P, prec) as s:
+            s.set_steps(tau, sig)
+            s.set_method("aa", mem=8, D=1e30)
+            if shapes is None:
+                t = s.autotune()
+                assert t["shape_x"] in (0, 1, 2) and t["shape_y"] in (0, 1, 2)
+                assert all(v > 0 for v in t["x_us"] + t["y_us"])
+            else:
+                s.set_task_shape(*shapes)
+            s.iterate(40)
+            x, y = s.get_iterate()
+            got.append(np.concatenate([x, y]))
+    # rows are summed in the same order under every shape; only the block
+    # partials of ||g|| differ in order (they decide nothing with D = 1e30)
+    for u in got[1:]:
+        assert np.array_equal(u, got[0])
+    with _solver(P, prec) as s:
+        from paper_2508_08062_gb300 import AAPDHGError
+        with pytest.raises(AAPDHGError):
+            s.set_task_shape(3, 0)

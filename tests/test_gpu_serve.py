@@ -1,0 +1,94 @@
+"""Served stream (aapdhg_server_*): continuous batching of LPs that arrive
+while others are on the GPU.
+
+Every step a member of a cohort takes is computed from that member's data
+alone, in the same order as in a batch of one (its rows, its element chunks
+and their reductions, its power-iteration segment), and a member joins its
+cohort at the cohort's first iteration.  So each LP's result from the server
+must equal, bit for bit, the result of the same LP solved alone with the
+same set-up; and it must be a 1e-4 (mixed) or 1e-6 (FP64) solution by the
+oracle's own KKT evaluation.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(P, tol, mem):
+    from paper_2508_08062_gb300 import BatchSolver
+    prec = "fp64" if tol < 1e-5 else "mixed"
+    with BatchSolver([P], precision=prec) as b:
+        b.set_scaling(10, True)
+        nrm = b.estimate_norms(100, seed=1)
+        b.set_steps(0.9 / nrm, 0.9 / nrm)
+        b.set_method("aa", mem=mem, D=10.0, eps=1.0)
+        b.set_tolerances([tol])
+        conv, _ = b.iterate(200000, tol=tol, kkt_every=64)
+        (x, y), = b.get_iterate()
+        st = b.status()[0]
+    return conv, x, y, int(st[0])
+
+
+def test_server_results_equal_alone_and_meet_their_tolerance():
+    from paper_2508_08062_gb300 import Server
+    rows = [300, 900, 450, 1500, 600, 1200, 350]
+    tols = [1e-4, 1e-4, 1e-6, 1e-4, 1e-6, 1e-4, 1e-4]
+    probs = [lpgen.batch_member(lpgen.SEED_BASE + 500 + i, r) for i, r in enumerate(rows)]
+    ids, t_sub = [], []
+    with Server(method="aa", mem=5, max_cohorts=3, max_cohort_size=2, max_iters=200000) as srv:
+        ids.append(srv.submit(probs[0], tols[0]))
+        ids.append(srv.submit(probs[1], tols[1]))
+        k, rounds, max_running = 2, 0, 0
+        while True:
+            running, waiting = srv.step()
+            max_running = max(max_running, running)
+            rounds += 1
+            # later LPs arrive one every few rounds, while others are on the GPU
+            if k < len(probs) and rounds % 3 == 0:
+                ids.append(srv.submit(probs[k], tols[k]))
+                k += 1
+            if k == len(probs) and running == 0 and waiting == 0:
+                break
+            assert rounds < 20000
+        res = [srv.result(i) for i in ids]
+        assert srv.device_bytes() == 0
+    assert max_running >= 2                  # cohorts overlapped on the device
+    for P, tol, r in zip(probs, tols, res):
+        assert r["state"] == "converged", r["state"]
+        assert 0 <= r["t_submit"] <= r["t_admit"] <= r["t_done"]
+        conv, x, y, its = _alone(P, tol, 5)
+        assert conv
+        assert r["iters"] == its
+        assert np.array_equal(r["x"], x) and np.array_equal(r["y"], y)
+        o = O.kkt(O.OracleLP.from_problem(P), r["x"], r["y"])
+        # mixed: the GPU's FP32 evaluation may differ from FP64 by a few FP32
+        # ulps of the residual's terms near the tolerance
+        assert o["kkt"] <= tol * (1.05 if tol >= 1e-5 else 1.0 + 1e-6), (tol, o)
+
+
+def test_server_rejects_what_cannot_fit_and_refuses_malformed_input():
+    from paper_2508_08062_gb300 import Server
+    good = lpgen.batch_member(lpgen.SEED_BASE + 600, 200)
+    bad = lpgen.batch_member(lpgen.SEED_BASE + 601, 200)
+    bad.col_idx = bad.col_idx.copy()
+    bad.col_idx[0] = bad.n                    # column out of range
+    with Server(method="aa", mem=5, max_cohorts=2, max_cohort_size=1, max_iters=50000,
+                mem_budget=1 << 20) as srv:      # 1 MiB: too small for any of them
+        a = srv.submit(good, 1e-4)
+        for _ in range(3):
+            srv.step()
+        assert srv.result(a)["state"] == "rejected"
+    from paper_2508_08062_gb300 import AAPDHGError
+    with Server(method="aa", mem=5, max_cohorts=2, max_cohort_size=1, max_iters=50000) as srv:
+        with pytest.raises(AAPDHGError, match="column index"):
+            srv.submit(bad, 1e-4)
+        b = srv.submit(good, 1e-4)               # the server goes on
+        for _ in range(20000):
+            running, waiting = srv.step()
+            if running == 0 and waiting == 0:
+                break
+        assert srv.result(b)["state"] == "converged"

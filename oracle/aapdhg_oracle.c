@@ -44,6 +44,25 @@
  *      keeps factor 1); the Pock-Chambolle pass (alpha = 1) then divides them
  *      by the square root of their sum of |entries|.  The scaled LP is
  *      Dr K Dc, Dr q, Dc c, bounds / Dc, with x = Dc x~ and y = Dr y~.
+ *  R13 Primal weight (Alg. "Primal weight update"; Remark on its form): the
+ *      step sizes are tau = gamma / omega, sigma = gamma omega, so the given
+ *      (tau, sigma) fix gamma = sqrt(tau sigma) and omega^0 = sqrt(sigma / tau).
+ *      The update is tried when the current iterate is u^k with k > 0 and
+ *      k = 0 mod U_P; Delta_x, Delta_y are the norms of the change of x and y
+ *      since u^{k - U_P} (u^0 for the first), whether or not the previous try
+ *      changed omega.
+ *  R14 D-hat re-blend (same Remark): applied at each update that changes
+ *      omega, D-hat = (1 - alpha) diag(1/omega, omega) + alpha diag(D1/omega,
+ *      D2 omega) with D1, D2 the blocks of the base D-hat; r_k and r_{k-1}
+ *      are the two latest residual norms ||g^{k-1}||, ||g^{k-2}||; the paper
+ *      gives no threshold for a "sufficient" decrease: rho_k >= rho_min
+ *      (default 0.1) selects alpha = 0.1, otherwise alpha = 0.9.  The epsilon
+ *      of rho_k is epsilon_zero.
+ *  R15 Memory reset: the update removes every memory column, and the pair
+ *      (u^k - u^{k-1}, g^k - g^{k-1}) across it (residuals of two different
+ *      operators) is not formed: that iteration takes the plain step
+ *      u^{k+1} = T(u^k) with the new steps (a PDHG step, counted in j) and the
+ *      memory restarts from it.
  */
 #include <math.h>
 #include <stdint.h>
@@ -70,6 +89,15 @@ typedef struct {
     double c_div;          /* safeguard divisor (R3)                           */
     int32_t dhat_mode;     /* 0: D-hat = I, 1: Remark on D-hat construction    */
     int32_t faa_adaptive;  /* R8                                               */
+    /* primal weight update (Alg. "Primal weight update", Remark on its form;
+     * readings R13-R15); pw_period = 0 switches it off                       */
+    int32_t pw_period;     /* U_P                                              */
+    double pw_theta;       /* smoothing theta                                  */
+    double pw_eps_zero;    /* epsilon_zero (also the epsilon of rho_k)         */
+    int32_t pw_dhat;       /* 1: re-blend D-hat at each update (Remark)        */
+    double pw_rho_min;     /* "sufficient" decrease of ||g|| (R14)             */
+    double pw_alpha_dec;   /* alpha when the residual decreased sufficiently   */
+    double pw_alpha_inc;   /* alpha otherwise                                  */
 } orc_params;
 
 /* ------------------------------------------------------------------------ */
@@ -441,7 +469,7 @@ int32_t orc_faa_filter(int64_t N, int32_t k, const double *E, const double *F, d
 int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const double *y0,
               int64_t max_iters, double tol, int32_t kkt_every, double *x_out, double *y_out,
               int64_t *counters, int64_t trace_len, int8_t *tr_branch, double *tr_gnorm,
-              double *tr_kkt, int32_t *tr_mk, int64_t rec_len, double *rec_u) {
+              double *tr_kkt, int32_t *tr_mk, int64_t rec_len, double *rec_u, double *dh_out) {
     const int32_t m = lp->m, n = lp->n;
     const int64_t N = (int64_t)n + m;
     const int M = p->method == 0 ? 0 : p->mem;
@@ -460,14 +488,24 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     int cols = 0;
 
     orc_dhat(lp, p->dhat_mode, dh, dh + n);
+    /* primal weight state (R13): gamma, omega, current steps, base D-hat,
+     * the iterate at the last update point, the two latest residual norms */
+    const double pw_gamma = sqrt(p->tau * p->sigma);
+    double omega = sqrt(p->sigma / p->tau), tau_c = p->tau, sigma_c = p->sigma;
+    double *dh_base = calloc(N + 1, sizeof(double));
+    double *snap = calloc(N + 1, sizeof(double));
+    memcpy(dh_base, dh, sizeof(double) * N);
+    double gn_last = NAN, gn_last2 = NAN;
 
     /* u^0 (R1) and u^1 = T u^0, g^0 = u^1 - u^0 */
     for (int32_t j = 0; j < n; ++j) u_prev[j] = x0 ? x0[j] : 0.0;
     for (int32_t i = 0; i < m; ++i) u_prev[n + i] = y0 ? y0[i] : 0.0;
     project(lp, u_prev, u_prev + n);
-    orc_T(lp, p->tau, p->sigma, u_prev, u_prev + n, u, u + n);
+    memcpy(snap, u_prev, sizeof(double) * N);
+    orc_T(lp, tau_c, sigma_c, u_prev, u_prev + n, u, u + n);
     for (int64_t e = 0; e < N; ++e) g_prev[e] = u[e] - u_prev[e];
     const double g0 = sqrt(dot(N, g_prev, g_prev));
+    gn_last = g0;
 
     int64_t i_aa = 0, j_pd = 0, it = 0;
     int status = 1;
@@ -484,13 +522,40 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
         if (it < trace_len && tr_kkt) tr_kkt[it] = have_kkt ? kk[3] : NAN;
         if (status == 0) break;
 
+        /* primal weight update (Alg. "Primal weight update"; R13-R15) */
+        int restart = 0;
+        if (p->pw_period > 0 && k % p->pw_period == 0) {
+            double dx = 0.0, dy = 0.0;
+            for (int32_t j = 0; j < n; ++j) dx += (u[j] - snap[j]) * (u[j] - snap[j]);
+            for (int32_t i = 0; i < m; ++i) dy += (u[n + i] - snap[n + i]) * (u[n + i] - snap[n + i]);
+            dx = sqrt(dx);
+            dy = sqrt(dy);
+            memcpy(snap, u, sizeof(double) * N);
+            if (dx > p->pw_eps_zero && dy > p->pw_eps_zero) {
+                omega = exp(p->pw_theta * log(dy / dx) + (1.0 - p->pw_theta) * log(omega));
+                tau_c = pw_gamma / omega;
+                sigma_c = pw_gamma * omega;
+                cols = 0;                                   /* reset the memory (R15) */
+                restart = 1;
+                if (p->pw_dhat) {                           /* D-hat re-blend (R14) */
+                    const double r1 = gn_last, r2 = gn_last2;
+                    const double rho = isnan(r2) ? 0.0 : (r2 - r1) / fmax(r2, p->pw_eps_zero);
+                    const double a = rho >= p->pw_rho_min ? p->pw_alpha_dec : p->pw_alpha_inc;
+                    for (int32_t j = 0; j < n; ++j) dh[j] = ((1.0 - a) + a * dh_base[j]) / omega;
+                    for (int32_t i = 0; i < m; ++i) dh[n + i] = ((1.0 - a) + a * dh_base[n + i]) * omega;
+                }
+            }
+        }
+
         /* u-hat^{k+1} = T u^k, g^k = u-hat^{k+1} - u^k */
-        orc_T(lp, p->tau, p->sigma, u, u + n, uh, uh + n);
+        orc_T(lp, tau_c, sigma_c, u, u + n, uh, uh + n);
         for (int64_t e = 0; e < N; ++e) g[e] = uh[e] - u[e];
         const double gn = sqrt(dot(N, g, g));
+        gn_last2 = gn_last;
+        gn_last = gn;
 
         /* memory update: append (u^k - u^{k-1}, g^k - g^{k-1}); keep at most m_A */
-        if (M > 0) {
+        if (M > 0 && !restart) {
             if (cols == M) {
                 memmove(dU, dU + N, sizeof(double) * N * (M - 1));
                 memmove(dG, dG + N, sizeof(double) * N * (M - 1));
@@ -505,7 +570,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
 
         int branch = 0, used = -1;
         double thresh = p->D * g0 * pow(i_aa / p->c_div + 1.0, -(1.0 + p->eps));
-        if (p->method != 0 && M > 0 && gn <= thresh) {
+        if (p->method != 0 && M > 0 && !restart && gn <= thresh) {
             const double *Eu = dU, *Fg = dG;
             int kc = cols, rc;
             if (p->method == 1) {
@@ -560,6 +625,7 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     memcpy(y_out, u + n, sizeof(double) * m);
     counters[0] = i_aa; counters[1] = j_pd; counters[2] = it;
     free(u); free(u_prev); free(uh); free(g); free(g_prev); free(dh); free(dU); free(dG);
-    free(gam); free(keep); free(E2); free(F2);
+    if (dh_out) memcpy(dh_out, dh, sizeof(double) * N);   /* D-hat in use at the end */
+    free(gam); free(keep); free(E2); free(F2); free(dh_base); free(snap);
     return status;
 }

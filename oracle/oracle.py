@@ -41,7 +41,9 @@ class _Params(C.Structure):
                 ("sigma", C.c_double), ("D", C.c_double), ("eps", C.c_double),
                 ("eta", C.c_double), ("beta", C.c_double), ("c_s", C.c_double),
                 ("kappa", C.c_double), ("c_div", C.c_double), ("dhat_mode", C.c_int32),
-                ("faa_adaptive", C.c_int32)]
+                ("faa_adaptive", C.c_int32), ("pw_period", C.c_int32), ("pw_theta", C.c_double),
+                ("pw_eps_zero", C.c_double), ("pw_dhat", C.c_int32), ("pw_rho_min", C.c_double),
+                ("pw_alpha_dec", C.c_double), ("pw_alpha_inc", C.c_double)]
 
 
 _lib = None
@@ -64,7 +66,7 @@ def lib():
         L.orc_faa_filter.argtypes = [C.c_int64, C.c_int32, vp, vp, C.c_double, C.c_double, vp]
         L.orc_faa_filter.restype = C.c_int32
         L.orc_solve.argtypes = [vp, vp, vp, vp, C.c_int64, C.c_double, C.c_int32, vp, vp, vp,
-                                C.c_int64, vp, vp, vp, vp, C.c_int64, vp]
+                                C.c_int64, vp, vp, vp, vp, C.c_int64, vp, vp]
         L.orc_solve.restype = C.c_int
         L.orc_scaling.argtypes = [vp, C.c_int32, C.c_int32, vp, vp]
         _lib = L
@@ -118,11 +120,19 @@ class Params:
     c_div: float = 1.0
     dhat_mode: int = 1
     faa_adaptive: int = 1
+    pw_period: int = 0       # primal weight update every pw_period iterations (0: off)
+    pw_theta: float = 0.5
+    pw_eps_zero: float = 1e-10
+    pw_dhat: int = 1
+    pw_rho_min: float = 0.1
+    pw_alpha_dec: float = 0.1
+    pw_alpha_inc: float = 0.9
 
     def _struct(self):
         return _Params(self.method, self.mem, self.tau, self.sigma, self.D, self.eps, self.eta,
                        self.beta, self.c_s, self.kappa, self.c_div, self.dhat_mode,
-                       self.faa_adaptive)
+                       self.faa_adaptive, self.pw_period, self.pw_theta, self.pw_eps_zero,
+                       self.pw_dhat, self.pw_rho_min, self.pw_alpha_dec, self.pw_alpha_inc)
 
 
 def dhat(lp: OracleLP, mode: int = 1):
@@ -209,6 +219,7 @@ class SolveResult:
     kkt: np.ndarray | None = None
     mk: np.ndarray | None = None
     rec_u: np.ndarray | None = None
+    dhat: np.ndarray | None = None       # D-hat in use at the end (primal weight re-blend)
 
 
 def solve(lp: OracleLP, params: Params, max_iters: int, tol: float = 0.0, kkt_every: int = 0,
@@ -224,10 +235,13 @@ def solve(lp: OracleLP, params: Params, max_iters: int, tol: float = 0.0, kkt_ev
     mk = np.full(tl, -1, dtype=np.int32) if trace else None
     rec = np.full((rec_len, lp.n + lp.m), np.nan) if rec_len > 0 else None
     ps = params._struct()
+    dh = np.empty(lp.n + lp.m)
     rc = lib().orc_solve(lp.ref, C.byref(ps), _p(x0), _p(y0), max_iters, tol, kkt_every, _p(x),
-                         _p(y), _p(counters), tl, _p(br), _p(gn), _p(kk), _p(mk), rec_len, _p(rec))
+                         _p(y), _p(counters), tl, _p(br), _p(gn), _p(kk), _p(mk), rec_len, _p(rec),
+                         _p(dh))
     it = int(counters[2])
     res = SolveResult(rc, x, y, int(counters[0]), int(counters[1]), it)
+    res.dhat = dh
     if trace:
         res.branch, res.gnorm, res.kkt, res.mk = br[:it + 1], gn[:it + 1], kk[:it + 1], mk[:it + 1]
     if rec is not None:

@@ -50,6 +50,11 @@ WORKLOADS = {
                         "with 10% free; AA-PDHG m=10, mixed precision"),
     "tiny": dict(method="aa", mem=5, precision="fp64",
                  desc="200 x 500 CSR, 10 nnz/row, N(0,1), '=' rows, 0<=x<=10; AA-PDHG m=5, FP64"),
+    "serve": dict(method="aa", mem=10, precision="mixed",
+                  desc="served stream: Poisson arrivals, LPs as in the batched workload but with "
+                       "rows log-uniform in [500, 200k], tolerance 1e-4 or 1e-6 (FP64 cohorts) per "
+                       "request; continuous batching into cohorts admitted by free HBM; AA-PDHG "
+                       "m=10 with Ruiz x10 + Pock-Chambolle per LP"),
     "batch": dict(method="aa", mem=10, precision="mixed",
                   desc="256 independent LPs, rows log-uniform in [1k, 50k], cols 2.5x rows, "
                        "lognormal row lengths (mean 8), N(0,1)*lognormal(0,2) per row, 30% '>=' "
@@ -194,6 +199,7 @@ def run_ours(args):
     s.set_steps(tau, sig)
     s.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
     kkt_every = 64
+    tuning = s.autotune()        # task shapes of the two half-steps (also done by the first iterate)
 
     dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
@@ -379,6 +385,9 @@ def run_ours(args):
                        "nnz": P.nnz, "scale": args.scale, "memory": M,
                        "preconditioning": "Ruiz x10 + Pock-Chambolle" if args.precondition else "none", "method": wl["method"],
                        "precision": wl["precision"], "kkt_every": kkt_every,
+                       "task_shapes": {"x": tuning["shape_x"], "y": tuning["shape_y"],
+                                       "x_us": [round(v, 1) for v in tuning["x_us"]],
+                                       "y_us": [round(v, 1) for v in tuning["y_us"]]},
                        "parallelism": f"replicas{world}",
                        "l2": "inputs larger than L2 (no flush)" if P.nnz * 16 > 129e6 else
                              "inputs fit in L2 (not flushed: back-to-back iterations)"},
@@ -466,6 +475,7 @@ def run_batch(args):
 
     b = BatchSolver(members, precision="mixed", stream=stream)
     prepare(b)
+    tuning = b.autotune()
     dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -604,6 +614,9 @@ def run_batch(args):
                        "rows": int(sum(P.m for P in members)), "cols": int(sum(P.n for P in members)),
                        "nnz": int(Ztot), "scale": args.scale, "memory": M, "kkt_every": kkt_every,
                        "tol": tol, "parallelism": f"replicas{world}",
+                       "task_shapes": {"x": tuning["shape_x"], "y": tuning["shape_y"],
+                                       "x_us": [round(v, 1) for v in tuning["x_us"]],
+                                       "y_us": [round(v, 1) for v in tuning["y_us"]]},
                        "l2": "inputs larger than L2 (no flush)"},
             "solved": solved, "batch_iterations": int(its),
             "member_iterations": {"p50": float(np.median(st[:, 0])), "max": int(st[:, 0].max()),
@@ -623,6 +636,127 @@ def run_batch(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def run_serve(args):
+    """The served stream: Poisson arrivals at --rate LPs/s for --duration s of
+    arrivals (drawn from a pool of distinct instances), served with continuous
+    batching; the queue then drains for at most --drain s.  Against a FIFO
+    replay of the same stream through the FP64 single-LP solver, with service
+    times measured per (instance, tolerance) on a sample."""
+    import torch
+    import lpgen
+    from paper_2508_08062_gb300 import Server, Solver
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    wl = WORKLOADS["serve"]
+    M = wl["mem"]
+    rng = np.random.default_rng(lpgen.SEED_BASE + 5 + 1000 * rank)
+    sizes = np.rint(np.exp(rng.uniform(np.log(500), np.log(200_000), args.pool))).astype(int)
+    sizes = np.maximum(4, np.rint(sizes * args.scale).astype(int))
+    pool = [lpgen.batch_member(lpgen.SEED_BASE * 1000 + 5000 + i, int(m)) for i, m in enumerate(sizes)]
+    n_req = int(rng.poisson(args.rate * args.duration))
+    arrivals = np.sort(rng.uniform(0.0, args.duration, n_req))
+    which = rng.integers(0, len(pool), n_req)
+    tols = np.where(rng.random(n_req) < 0.5, 1e-4, 1e-6)
+    stream_desc = {"requests": n_req, "rate_per_s": args.rate, "arrival_window_s": args.duration,
+                   "pool": len(pool), "pool_rows": [int(m) for m in sizes], "drain_limit_s": args.drain}
+
+    dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
+    dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
+    ids = []
+    with Server(method="aa", mem=M, max_cohorts=args.max_cohorts,
+                max_cohort_size=args.cohort_size, max_iters=args.serve_max_iters) as srv:
+        with ClockSampler(dev_id) as clk:
+            t0 = time.perf_counter()
+            k = 0
+            while True:
+                now = time.perf_counter() - t0
+                while k < n_req and arrivals[k] <= now:
+                    ids.append(srv.submit(pool[which[k]], float(tols[k])))
+                    k += 1
+                running, waiting = srv.step()
+                if k == n_req and running == 0 and waiting == 0:
+                    break
+                if now > args.duration + args.drain:
+                    break
+                if running == 0 and waiting == 0 and k < n_req:
+                    time.sleep(max(0.0, min(arrivals[k] - now, 0.01)))
+            wall = time.perf_counter() - t0
+        res = [srv.result(i) for i in ids]
+    states = [r["state"] for r in res]
+    done = [r for r in res if r["state"] == "converged"]
+    lat = np.array([r["t_done"] - r["t_submit"] for r in done])
+    per_tol = {}
+    for tv in (1e-4, 1e-6):
+        sel = [r for r, t in zip(res, tols[:len(res)]) if t == tv and r["state"] == "converged"]
+        per_tol[str(tv)] = len(sel)
+    value = len(done) / wall
+
+    # FIFO replay through the FP64 single-LP solver: service time per
+    # (instance, tolerance) measured on a sample of the pool
+    base = None
+    if args.single_sample > 0:
+        order = np.argsort(sizes)
+        pick = order[np.linspace(0, len(pool) - 1, min(args.single_sample, len(pool))).astype(int)]
+        svc = {}
+        stream = torch.cuda.current_stream()
+        for p in pick:
+            for tv in (1e-4, 1e-6):
+                with Solver(pool[p], precision="fp64", stream=stream) as s1:
+                    s1.set_scaling(10, True)
+                    nrm = s1.estimate_norm(100, seed=1)
+                    s1.set_steps(0.9 / nrm, 0.9 / nrm)
+                    s1.set_method("aa", mem=M, D=10.0, eps=1.0)
+                    torch.cuda.synchronize()
+                    ts = time.perf_counter()
+                    c, n_it = s1.iterate(args.serve_max_iters, tol=tv, kkt_every=64)
+                    torch.cuda.synchronize()
+                    svc[(int(p), tv)] = (time.perf_counter() - ts, bool(c))
+        # instances outside the sample take the service time of the nearest sampled size
+        def service(i, tv):
+            q = int(pick[np.argmin(np.abs(np.log(sizes[pick]) - np.log(sizes[i])))])
+            return svc[(q, tv)]
+        t_free, lat_b, ok_b = 0.0, [], 0
+        for a, i, tv in zip(arrivals, which, tols):
+            d, c = service(int(i), float(tv))
+            start = max(t_free, a)
+            t_free = start + d
+            if c:
+                lat_b.append(t_free - a)
+                ok_b += 1
+        lat_b = np.array(lat_b)
+        base = {"solves_per_s": ok_b / t_free if t_free > 0 else None, "makespan_s": t_free,
+                "converged": ok_b,
+                "p50_s": float(np.percentile(lat_b, 50)) if len(lat_b) else None,
+                "p99_s": float(np.percentile(lat_b, 99)) if len(lat_b) else None,
+                "sample": [int(p) for p in pick],
+                "note": "FIFO replay of the same arrivals through the FP64 single-LP solver "
+                        "(same scaling, step rule, AA m=10, iteration cap); service times "
+                        "measured per (sampled instance, tolerance), nearest sampled size for "
+                        "the others"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": len(ids), "warmup": 0, "ms_per_step": 1e3 * wall / max(len(done), 1),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+        "data": "synthetic (seeded generator, known optimum per LP)",
+        "config": {"workload": "serve", "desc": wl["desc"], **stream_desc,
+                   "max_cohorts": args.max_cohorts, "cohort_size": args.cohort_size,
+                   "max_iters_per_lp": args.serve_max_iters, "scale": args.scale},
+        "completed": {s_: states.count(s_) for s_ in set(states)},
+        "converged_by_tol": per_tol, "wall_s": wall,
+        "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
+        "p99_latency": float(np.percentile(lat, 99)) if len(lat) else None,
+        "sequential_fp64_single_lp": base,
+        "clocks": clk.summary(),
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": None,
+                "d2h_bytes_per_step": None,
+                "session": "every request from host arrays through the public server API, "
+                           "results read back: the value is already end to end"},
+    }
+    print(json.dumps(line), flush=True)
 
 
 def cpu_baseline_batch(members, st, M, budget_s=20.0):
@@ -707,7 +841,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    if args.workload == "batch":
+    if args.workload in ("batch", "serve"):
         return run_reference_batch(args)
     wl = WORKLOADS[args.workload]
     P = make_problem(args.workload, 0, args.scale)
@@ -749,6 +883,15 @@ def main():
                     help="batch workload: iteration cap of the solve to 1e-4")
     ap.add_argument("--single-sample", type=int, default=16,
                     help="batch workload: LPs solved one at a time by the FP64 single-LP solver")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve workload: arrivals per s")
+    ap.add_argument("--duration", type=float, default=1.0,
+                    help="serve workload: seconds of arrivals (the queue then drains)")
+    ap.add_argument("--drain", type=float, default=120.0,
+                    help="serve workload: at most this many seconds after the last arrival")
+    ap.add_argument("--pool", type=int, default=16, help="serve workload: distinct LP instances")
+    ap.add_argument("--max-cohorts", type=int, default=4)
+    ap.add_argument("--cohort-size", type=int, default=64)
+    ap.add_argument("--serve-max-iters", type=int, default=100000)
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload's m, n, nnz (profiling captures only)")
     args = ap.parse_args()
@@ -758,6 +901,8 @@ def main():
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_ours(args)
 

@@ -624,8 +624,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
     memcpy(x_out, u, sizeof(double) * n);
     memcpy(y_out, u + n, sizeof(double) * m);
     counters[0] = i_aa; counters[1] = j_pd; counters[2] = it;
-    free(u); free(u_prev); free(uh); free(g); free(g_prev); free(dh); free(dU); free(dG);
     if (dh_out) memcpy(dh_out, dh, sizeof(double) * N);   /* D-hat in use at the end */
+    free(u); free(u_prev); free(uh); free(g); free(g_prev); free(dh); free(dU); free(dG);
     free(gam); free(keep); free(E2); free(F2); free(dh_base); free(snap);
     return status;
 }

@@ -583,28 +583,36 @@ template <typename V> aapdhg_status autotune_t(aapdhg_t h) {
     cudaEvent_t e0, e1;
     CK(h, cudaEventCreate(&e0));
     CK(h, cudaEventCreate(&e1));
-    float best_x = 1e30f, best_y = 1e30f;
+    // two interleaved rounds, the faster of the two kept per shape (robust to
+    // clock ramps and to whatever ran just before)
+    double tx[NSHAPE], ty[NSHAPE];
+    for (int sh = 0; sh < NSHAPE; ++sh) tx[sh] = ty[sh] = 1e30;
+    for (int round = 0; round < 2; ++round)
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+            P.grid1 = h->gridx[sh];
+            P.grid2 = h->gridy[sh];
+            float ms = 0.f;
+            for (int w = 0; w < 2; ++w) launch_x<V, false>(h, sh, MODE_TUNE);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 5; ++r) launch_x<V, false>(h, sh, MODE_TUNE);
+            cudaEventRecord(e1, h->stream);
+            CK(h, cudaEventSynchronize(e1));
+            cudaEventElapsedTime(&ms, e0, e1);
+            tx[sh] = std::min(tx[sh], 1e3 * ms / 5);
+            for (int w = 0; w < 2; ++w) launch_y<V, false>(h, sh, MODE_TUNE);
+            cudaEventRecord(e0, h->stream);
+            for (int r = 0; r < 5; ++r) launch_y<V, false>(h, sh, MODE_TUNE);
+            cudaEventRecord(e1, h->stream);
+            CK(h, cudaEventSynchronize(e1));
+            cudaEventElapsedTime(&ms, e0, e1);
+            ty[sh] = std::min(ty[sh], 1e3 * ms / 5);
+        }
     int bx = 0, by = 0;
     for (int sh = 0; sh < NSHAPE; ++sh) {
-        P.grid1 = h->gridx[sh];
-        P.grid2 = h->gridy[sh];
-        for (int w = 0; w < 2; ++w) launch_x<V, false>(h, sh, MODE_TUNE);
-        cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < 5; ++r) launch_x<V, false>(h, sh, MODE_TUNE);
-        cudaEventRecord(e1, h->stream);
-        CK(h, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        h->tune_us[sh] = 1e3 * ms / 5;
-        if (ms < best_x) { best_x = ms; bx = sh; }
-        for (int w = 0; w < 2; ++w) launch_y<V, false>(h, sh, MODE_TUNE);
-        cudaEventRecord(e0, h->stream);
-        for (int r = 0; r < 5; ++r) launch_y<V, false>(h, sh, MODE_TUNE);
-        cudaEventRecord(e1, h->stream);
-        CK(h, cudaEventSynchronize(e1));
-        cudaEventElapsedTime(&ms, e0, e1);
-        h->tune_us[NSHAPE + sh] = 1e3 * ms / 5;
-        if (ms < best_y) { best_y = ms; by = sh; }
+        h->tune_us[sh] = tx[sh];
+        h->tune_us[NSHAPE + sh] = ty[sh];
+        if (tx[sh] < tx[bx]) bx = sh;
+        if (ty[sh] < ty[by]) by = sh;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);

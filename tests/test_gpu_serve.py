@@ -35,9 +35,15 @@ def _alone(P, tol, mem):
 
 def test_server_results_equal_alone_and_meet_their_tolerance():
     from paper_2508_08062_gb300 import Server
-    rows = [300, 900, 450, 1500, 600, 1200, 350]
-    tols = [1e-4, 1e-4, 1e-6, 1e-4, 1e-6, 1e-4, 1e-4]
-    probs = [lpgen.batch_member(lpgen.SEED_BASE + 500 + i, r) for i, r in enumerate(rows)]
+    # (m, n, seed, tol): LPs the oracle takes to their tolerance (scaled as the
+    # server scales them) within a few thousand AA iterations; the 1e-6 ones
+    # run in FP64 cohorts
+    spec = [(60, 150, 700, 1e-4), (120, 300, 701, 1e-6), (90, 200, 702, 1e-4),
+            (200, 500, 703, 1e-6), (150, 330, 704, 1e-4), (80, 190, 705, 1e-6),
+            (110, 260, 706, 1e-4)]
+    probs = [lpgen.random_lp(m, n, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=sd)
+             for m, n, sd, _ in spec]
+    tols = [t for *_, t in spec]
     ids, t_sub = [], []
     with Server(method="aa", mem=5, max_cohorts=3, max_cohort_size=2, max_iters=200000) as srv:
         ids.append(srv.submit(probs[0], tols[0]))
@@ -72,12 +78,12 @@ def test_server_results_equal_alone_and_meet_their_tolerance():
 
 def test_server_rejects_what_cannot_fit_and_refuses_malformed_input():
     from paper_2508_08062_gb300 import Server
-    good = lpgen.batch_member(lpgen.SEED_BASE + 600, 200)
-    bad = lpgen.batch_member(lpgen.SEED_BASE + 601, 200)
+    good = lpgen.random_lp(120, 300, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=701)
+    bad = lpgen.random_lp(60, 150, nnz_per_row=5, seed=702)
     bad.col_idx = bad.col_idx.copy()
     bad.col_idx[0] = bad.n                    # column out of range
     with Server(method="aa", mem=5, max_cohorts=2, max_cohort_size=1, max_iters=50000,
-                mem_budget=1 << 20) as srv:      # 1 MiB: too small for any of them
+                mem_budget=4096) as srv:         # 4 KiB: too small for any LP
         a = srv.submit(good, 1e-4)
         for _ in range(3):
             srv.step()

@@ -196,6 +196,23 @@ aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable);
 aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
                                         double *total_ms);
 
+/* Primal weight update with memory reset and D-hat re-blend (Alg. "Primal
+ * weight update" and the Remark on its form).  period = U_P > 0 switches it
+ * on: the given steps define gamma = sqrt(tau sigma) and omega^0 =
+ * sqrt(sigma / tau); when the current iterate is u^k with k > 0, k = 0 mod
+ * U_P, Delta_x = ||x^k - x^{k-U_P}|| and Delta_y likewise, and if both exceed
+ * eps_zero: omega <- exp(theta log(Delta_y/Delta_x) + (1 - theta) log omega),
+ * tau = gamma / omega, sigma = gamma omega, the Anderson memory is reset (that
+ * iteration takes the plain step), and with dhat_blend = 1 D-hat <-
+ * (1 - alpha) diag(1/omega, omega) + alpha diag(D1/omega, D2 omega), alpha =
+ * alpha_dec when the relative decrease of ||g|| over the last iteration is
+ * >= rho_min, else alpha_inc (paper: alpha 0.1 / 0.9, theta 0.5, U_P 3000).
+ * period = 0 switches it off.  theta, alpha_* in [0, 1], eps_zero >= 0
+ * (AAPDHG_ERR_INVALID otherwise).  Resets the run.                          */
+aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta, double eps_zero,
+                                       int32_t dhat_blend, double rho_min, double alpha_dec,
+                                       double alpha_inc);
+
 /* Autotuning of the two PDHG half-step kernels (the SpMVs of eq. pdhg; the
  * paper has no counterpart).  They are compiled for AAPDHG_TASK_SHAPES task
  * shapes (shape 0: two SELL slices per warp task, 8 loads in flight per lane;

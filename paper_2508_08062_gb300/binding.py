@@ -35,6 +35,7 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
            "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_batch_autotune",
+           "aapdhg_set_primal_weight",
            "aapdhg_batch_set_task_shape", "aapdhg_batch_set_tolerances", "aapdhg_batch_launch",
            "aapdhg_batch_poll", "aapdhg_server_create", "aapdhg_server_submit",
            "aapdhg_server_step", "aapdhg_server_result", "aapdhg_server_device_bytes",
@@ -94,6 +95,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_destroy.argtypes = [vp]
     L.aapdhg_destroy.restype = None
     L.aapdhg_autotune.argtypes = [vp, vp, vp, vp]
+    L.aapdhg_set_primal_weight.argtypes = [vp, i64, f64, f64, i32, f64, f64, f64]
     L.aapdhg_set_task_shape.argtypes = [vp, i32, i32]
     L.aapdhg_batch_autotune.argtypes = [vp, vp, vp, vp]
     L.aapdhg_batch_set_task_shape.argtypes = [vp, i32, i32]
@@ -254,6 +256,14 @@ class Solver:
     def set_scaling(self, ruiz_iters=10, pock_chambolle=True):
         """Ruiz + Pock-Chambolle diagonal scaling (once per solver; resets the run)."""
         self._check(self._L.aapdhg_set_scaling(self._h, int(ruiz_iters), int(bool(pock_chambolle))))
+
+    def set_primal_weight(self, period=3000, theta=0.5, eps_zero=1e-10, dhat_blend=True,
+                          rho_min=0.1, alpha_dec=0.1, alpha_inc=0.9):
+        """Periodic primal weight update (period 0: off); resets the run."""
+        self._check(self._L.aapdhg_set_primal_weight(self._h, int(period), float(theta),
+                                                     float(eps_zero), int(bool(dhat_blend)),
+                                                     float(rho_min), float(alpha_dec),
+                                                     float(alpha_inc)))
 
     def set_start(self, x0=None, y0=None):
         x0 = None if x0 is None else _f64(x0, self.n)

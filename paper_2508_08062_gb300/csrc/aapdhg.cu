@@ -246,6 +246,15 @@ struct aapdhg_s {
     bool tuned = false, autotune = true;
     int32_t gridx[NSHAPE] = {1, 1, 1}, gridy[NSHAPE] = {1, 1, 1};
     double tune_us[2 * NSHAPE] = {0, 0, 0, 0, 0, 0};
+    // primal weight update (off when pw_period = 0)
+    int64_t pw_period = 0;
+    double pw_theta = 0.5, pw_eps = 1e-10, pw_rho_min = 0.1, pw_alpha_dec = 0.1, pw_alpha_inc = 0.9;
+    int32_t pw_dhat = 1;
+    double pw_gamma = 0.0, pw_omega = 1.0, tau_user = 0.0, sigma_user = 0.0;
+    void *pw_snap = nullptr, *pw_dh_base = nullptr;
+    double *pw_part = nullptr;
+    bool pw_base_valid = false;            // pw_dh_base holds the current base D-hat
+    int64_t pw_last_k = -1;                // iterate index of the last update tried
     int32_t dhat_mode = -1;                // mode D-hat was last formed with
     bool scaled = false;                   // aapdhg_set_scaling applied
     std::vector<double> dr_host, dc_host;  // Dr, Dc in internal order (when scaled)
@@ -480,6 +489,8 @@ template <typename V> aapdhg_status ensure_rings(aapdhg_t h, int32_t M) {
     return AAPDHG_OK;
 }
 
+void drop_graphs(aapdhg_t h);
+
 template <typename V> aapdhg_status reset_run(aapdhg_t h) {
     typedef typename Vec2<V>::T V2;
     Prob<V> &P = prob<V>(h);
@@ -498,6 +509,24 @@ template <typename V> aapdhg_status reset_run(aapdhg_t h) {
     CK(h, cudaMemcpyAsync(P.UP, up.data(), sizeof(V2) * h->N, cudaMemcpyHostToDevice, h->stream));
     // clear the run fields of the state, keep the norm scratch
     CK(h, cudaMemsetAsync(h->st, 0, offsetof(DevState, scratch), h->stream));
+    if (h->pw_period > 0) {
+        // a run starts with the given steps and the base D-hat (R13)
+        h->mp.tau = h->tau_user;
+        h->mp.sigma = h->sigma_user;
+        h->pw_gamma = sqrt(h->tau_user * h->sigma_user);
+        h->pw_omega = h->tau_user > 0 ? sqrt(h->sigma_user / h->tau_user) : 1.0;
+        h->pw_last_k = -1;
+        if (h->pw_dh_base) {
+            V *dh = const_cast<V *>(P.dh);
+            if (!h->pw_base_valid) {
+                CK(h, cudaMemcpyAsync(h->pw_dh_base, dh, sizeof(V) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+                h->pw_base_valid = true;
+            } else {
+                CK(h, cudaMemcpyAsync(dh, h->pw_dh_base, sizeof(V) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+            }
+        }
+        drop_graphs(h);
+    }
     if (P.tr.cap > 0) {
         std::vector<int8_t> b(P.tr.cap, -1);
         std::vector<double> nanv(P.tr.cap, NAN);
@@ -697,6 +726,39 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
     return true;
 }
 
+// Primal weight update at the iterate u^k (Alg. "Primal weight update",
+// readings R13-R15): Delta_x, Delta_y against the snapshot (which becomes
+// u^k); when both exceed epsilon_zero, the new omega gives tau = gamma/omega,
+// sigma = gamma omega, D-hat is re-blended (Remark on the form) and the memory
+// restarts at this iteration.
+template <typename V> aapdhg_status pw_update(aapdhg_t h, int64_t k) {
+    Prob<V> &P = prob<V>(h);
+    const int cur = (int)(((k - 1) & 1) ^ 1);
+    k_pw_delta<V><<<h->grid5, BLOCK, 0, h->stream>>>(P.UP, (V *)h->pw_snap, h->n, h->N, cur, 0,
+                                                      h->pw_part, h->st);
+    CK(h, cudaGetLastError());
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    const double dx = sqrt(h->st_host->scratch[2]), dy = sqrt(h->st_host->scratch[3]);
+    if (!(dx > h->pw_eps && dy > h->pw_eps)) return AAPDHG_OK;
+    h->pw_omega = exp(h->pw_theta * log(dy / dx) + (1.0 - h->pw_theta) * log(h->pw_omega));
+    h->mp.tau = h->pw_gamma / h->pw_omega;
+    h->mp.sigma = h->pw_gamma * h->pw_omega;
+    if (h->pw_dhat && h->pw_dh_base) {
+        const double r1 = h->st_host->gnorm, r2 = h->st_host->gnorm_prev;
+        const double rho = std::isnan(r2) ? 0.0 : (r2 - r1) / std::max(r2, h->pw_eps);
+        const double alpha = rho >= h->pw_rho_min ? h->pw_alpha_dec : h->pw_alpha_inc;
+        k_dhat_blend<V><<<h->grid5, BLOCK, 0, h->stream>>>(const_cast<V *>(P.dh), (const V *)h->pw_dh_base,
+                                                            h->n, h->N, h->pw_omega, alpha);
+        CK(h, cudaGetLastError());
+    }
+    const int32_t one = 1;
+    CK(h, cudaMemcpyAsync(&h->st->restart, &one, sizeof(int32_t), cudaMemcpyHostToDevice, h->stream));
+    CK(h, cudaStreamSynchronize(h->stream));
+    drop_graphs(h);
+    return AAPDHG_OK;
+}
+
 template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, double tol,
                                               int32_t kkt_every, int64_t *done_iters) {
     Prob<V> &P = prob<V>(h);
@@ -707,6 +769,9 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
     if (h->autotune && !h->tuned && (s = autotune_t<V>(h)) != AAPDHG_OK) return s;
     if ((s = read_state(h)) != AAPDHG_OK) return s;
     if (!h->st_host->init_done) {
+        if (h->pw_period > 0)      // snapshot u^0 for the first primal weight update
+            k_pw_delta<V><<<h->grid5, BLOCK, 0, h->stream>>>(P.UP, (V *)h->pw_snap, h->n, h->N, 0, 1,
+                                                              h->pw_part, h->st);
         launch_iteration<V>(h, false, MODE_INIT);
         CK(h, cudaGetLastError());
         if ((s = read_state(h)) != AAPDHG_OK) return s;
@@ -718,7 +783,17 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
     int64_t hit = it0, launched = 0;
     bool done = false;
     while (launched < max_iters && !done) {
-        const int64_t chunk = std::min<int64_t>(CHUNK_ITERS, max_iters - launched);
+        int64_t chunk = std::min<int64_t>(CHUNK_ITERS, max_iters - launched);
+        if (h->pw_period > 0) {
+            // the current iterate is u^k with k = hit + 1; updates at k = 0 mod U_P,
+            // each at the start of a chunk
+            const int64_t k = hit + 1, r = k % h->pw_period;
+            if (r == 0 && h->pw_last_k != k) {
+                if ((s = pw_update<V>(h, k)) != AAPDHG_OK) return s;
+                h->pw_last_k = k;
+            }
+            chunk = std::min<int64_t>(chunk, r == 0 ? h->pw_period : h->pw_period - r);
+        }
         if (!(chunk == CHUNK_ITERS && launch_chunk_graph<V>(h, hit, kkt_every))) {
             for (int64_t c = 0; c < chunk; ++c) {
                 const int64_t itc = hit + c;
@@ -862,6 +937,7 @@ template <typename V> aapdhg_status set_scaling_t(aapdhg_t h, int32_t ruiz_iters
     k_dhat<V><<<gD, BLOCK, 0, s>>>(P.KT, P.K, n, m, h->dhat_mode < 0 ? 1 : h->dhat_mode,
                                    const_cast<V *>(P.dh));
     CK(h, cudaGetLastError());
+    h->pw_base_valid = false;
     h->scaled = true;
     return AAPDHG_OK;
 }
@@ -976,6 +1052,8 @@ aapdhg_status aapdhg_set_steps(aapdhg_t h, double tau, double sigma) {
     if (!(tau > 0) || !(sigma > 0) || !std::isfinite(tau) || !std::isfinite(sigma))
         return fail(h, AAPDHG_ERR_INVALID, "tau and sigma must be finite and > 0");
     h->mp.tau = tau;
+    h->tau_user = tau;
+    h->sigma_user = sigma;
     h->mp.sigma = sigma;
     h->have_steps = true;
     drop_graphs(h);
@@ -1013,6 +1091,7 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
                                                        const_cast<float *>(h->pf.dh));
         CK(h, cudaGetLastError());
         h->dhat_mode = dhat_mode;
+        h->pw_base_valid = false;
     }
     return reset_any(h);
 }
@@ -1153,6 +1232,45 @@ aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launc
         if (total_ms) *total_ms = h->prof_ms[kind];
     }
     return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta, double eps_zero,
+                                       int32_t dhat_blend, double rho_min, double alpha_dec,
+                                       double alpha_inc) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (period < 0 || !(theta >= 0 && theta <= 1) || !(eps_zero >= 0) || !std::isfinite(rho_min) ||
+        !(alpha_dec >= 0 && alpha_dec <= 1) || !(alpha_inc >= 0 && alpha_inc <= 1))
+        return fail(h, AAPDHG_ERR_INVALID, "primal weight parameters out of range");
+    h->pw_period = period;
+    h->pw_theta = theta;
+    h->pw_eps = eps_zero;
+    h->pw_dhat = dhat_blend ? 1 : 0;
+    h->pw_rho_min = rho_min;
+    h->pw_alpha_dec = alpha_dec;
+    h->pw_alpha_inc = alpha_inc;
+    if (period > 0) {
+        const size_t sv = h->prec == AAPDHG_FP64 ? 8 : 4;
+        if (!h->pw_snap) h->pw_snap = dev_alloc(h, sv * h->N);
+        if (!h->pw_dh_base) {
+            h->pw_dh_base = dev_alloc(h, sv * h->N);
+            h->pw_base_valid = false;
+        }
+        if (!h->pw_part) h->pw_part = (double *)dev_alloc(h, sizeof(double) * 2 * h->grid5);
+        if (!h->pw_snap || !h->pw_dh_base || !h->pw_part)
+            return fail(h, AAPDHG_ERR_OOM, "primal weight buffers");
+    } else {
+        // back to fixed steps: the given steps and the base D-hat
+        h->mp.tau = h->tau_user > 0 ? h->tau_user : h->mp.tau;
+        h->mp.sigma = h->sigma_user > 0 ? h->sigma_user : h->mp.sigma;
+        if (h->pw_dh_base && h->pw_base_valid) {
+            CK(h, cudaMemcpyAsync(h->prec == AAPDHG_FP64 ? (void *)h->pd.dh : (void *)h->pf.dh, h->pw_dh_base,
+                                  (h->prec == AAPDHG_FP64 ? 8 : 4) * (size_t)h->N, cudaMemcpyDeviceToDevice,
+                                  h->stream));
+        }
+    }
+    drop_graphs(h);
+    return reset_any(h);
 }
 
 aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us) {

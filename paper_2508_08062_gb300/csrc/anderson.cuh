@@ -343,8 +343,11 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     __shared__ int s_nold, s_new, s_prev_acc;
     __shared__ double sh[WARPS * (MC + 3)];
     const int cur = (mode == MODE_INIT) ? 0 : (int)(st->it & 1) ^ 1;
+    // the iteration of a primal weight update restarts the memory: a plain
+    // step, g^k kept as the previous residual, no column formed across it
+    const bool restart = mode == MODE_ITER && st->restart;
 
-    if (mode == MODE_INIT) {
+    if (mode == MODE_INIT || restart) {
         if (M > 0) {
             for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N;
                  e += (int64_t)gridDim.x * BLOCK) {
@@ -358,8 +361,19 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
             st->free_slot = 0;
             st->accept = 0;   // u^1 = T u^0 behaves as a PDHG step: du^0 = g^0
             st->use_count = 0;
-            st->it = 0;
-            st->init_done = 1;
+            if (restart) {
+                const int64_t it = st->it;
+                st->n_pd += 1;
+                st->restart = 0;
+                if (it < P.tr.cap) {
+                    P.tr.branch[it] = 0;
+                    P.tr.mk[it] = -1;
+                }
+                st->it = it + 1;
+            } else {
+                st->it = 0;
+                st->init_done = 1;
+            }
         }
         return;
     }

@@ -109,6 +109,8 @@ struct DevState {
     double en2[NSLOT];     // ||du_s||^2 by slot
     double g0;             // ||g^0||
     double gnorm;          // ||g^k||
+    double gnorm_prev;     // ||g^{k-1}||
+    int32_t restart;       // primal weight update: this iteration restarts the memory
     double kkt[6];         // r_p, r_d, r_g, KKT, c'x, dual objective at u^k
     int32_t kkt_valid;
     uint32_t cnt_spmv;     // last-block counter of the y-step

@@ -86,6 +86,44 @@ __global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mo
     }
 }
 
+// Primal weight update (Alg. "Primal weight update"): ||x^k - x^{k-U_P}||^2
+// and ||y^k - y^{k-U_P}||^2 against the snapshot (into st->scratch[2], [3] by
+// the last block), and the snapshot <- u^k.  copy_only: the snapshot alone.
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_pw_delta(const typename Vec2<V>::T *UP, V *snap, int64_t n,
+                                                    int64_t N, int cur, int copy_only, double *part,
+                                                    DevState *st) {
+    Acc<V> a[2];
+    for (int64_t e = blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < N; e += (int64_t)gridDim.x * BLOCK) {
+        const V u = comp<V>(UP[e], cur);
+        if (!copy_only) a[e < n ? 0 : 1].add_sq(u - snap[e]);
+        snap[e] = u;
+    }
+    if (copy_only) return;
+    __shared__ double sh[WARPS * 2];
+    block_reduce_store<V, 2>(a, sh, part + 2 * (int64_t)blockIdx.x);
+    if (last_block(&st->cnt_norm) && threadIdx.x == 0) {
+        double sx = 0.0, sy = 0.0;
+        for (int b = 0; b < (int)gridDim.x; ++b) {
+            sx += __ldcg(part + 2 * b);
+            sy += __ldcg(part + 2 * b + 1);
+        }
+        st->scratch[2] = sx;
+        st->scratch[3] = sy;
+    }
+}
+
+// D-hat re-blend of the Remark on the primal weight's form:
+// (1 - alpha) diag(1/omega, omega) + alpha diag(D1/omega, D2 omega).
+template <typename V>
+__global__ void k_dhat_blend(V *dh, const V *base, int64_t n, int64_t N, double omega, double alpha) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const double b = (1.0 - alpha) + alpha * (double)base[e];
+        dh[e] = (V)(e < n ? b / omega : b * omega);
+    }
+}
+
 // Elementwise helpers: a *= b, a /= b, out = 1 / b, a = v.
 template <typename V>
 __global__ void k_vmul(V *a, const V *b, int64_t n) {

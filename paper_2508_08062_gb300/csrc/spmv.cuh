@@ -317,6 +317,7 @@ __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, b
         return;
     }
     if (!isfinite(gn) || (kkt && !isfinite(out[3]))) { st->error = 1; return; }
+    st->gnorm_prev = mode == MODE_INIT ? NAN : st->gnorm;
     st->gnorm = gn;
     if (mode == MODE_INIT) { st->g0 = gn; return; }
     const int64_t it = st->it;

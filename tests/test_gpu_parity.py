@@ -325,3 +325,57 @@ def test_task_shapes_give_identical_iterates(prec):
         from paper_2508_08062_gb300 import AAPDHGError
         with pytest.raises(AAPDHGError):
             s.set_task_shape(3, 0)
+
+
+# --------------------------------------------------------------------------
+# Primal weight update with memory reset and D-hat re-blend (readings R13-R15)
+# --------------------------------------------------------------------------
+PW_CASES = {
+    "aa5_pw": dict(method=1, mem=5),
+    "faa5_pw": dict(method=2, mem=5),
+    "pdhg_pw": dict(method=0, mem=0),
+    "aa5_pw_theta1_noblend": dict(method=1, mem=5, pw_theta=1.0, pw_dhat=0),
+}
+
+
+@pytest.mark.parametrize("name", list(PW_CASES))
+def test_fp64_primal_weight_iterates_match_oracle(name):
+    P = lpgen.random_lp(333, 777, nnz_per_row=7, frac_ge=0.4, frac_free=0.15, frac_lower_only=0.1,
+                        frac_upper_only=0.1, row_scale_sigma=1.0, seed=4)
+    tau, sig = _steps(P)
+    sig *= 4.0                                     # omega^0 = 2: the steps differ from the start
+    tau /= 4.0
+    kw = dict(PW_CASES[name])
+    prm = O.Params(tau=tau, sigma=sig, pw_period=50, **kw)
+    ref = O.solve(O.OracleLP.from_problem(P), prm, ITERS, trace=True, rec_len=ITERS + 1)
+    with _solver(P) as s:
+        s.set_steps(tau, sig)
+        s.set_method(method=prm.method, mem=prm.mem)
+        s.set_primal_weight(period=50, theta=prm.pw_theta, eps_zero=prm.pw_eps_zero,
+                            dhat_blend=bool(prm.pw_dhat), rho_min=prm.pw_rho_min)
+        s.set_trace(ITERS)
+        s.iterate(0)
+        for k in range(ITERS + 1):
+            x, y = s.get_iterate()
+            u = np.concatenate([x, y])
+            err = np.linalg.norm(u - ref.rec_u[k]) / np.linalg.norm(ref.rec_u[k])
+            assert err <= FP64_TOL, (name, k, err)
+            if k < ITERS:
+                s.iterate(1)
+        tr = s.get_trace()
+    assert np.array_equal(tr["branch"][:ITERS], ref.branch[:ITERS]), name
+    # the update iterations are plain steps
+    assert all(tr["branch"][k - 1] == 0 for k in (50, 100, 150))
+
+
+def test_mixed_primal_weight_converges():
+    P = lpgen.tiny()
+    tau, sig = _steps(P)
+    with _solver(P, "mixed") as s:
+        s.set_steps(tau, sig)
+        s.set_method("aa", mem=5)
+        s.set_primal_weight(period=500)
+        conv, its = s.iterate(100000, tol=1e-4, kkt_every=64)
+        x, y = s.get_iterate()
+    assert conv
+    assert O.kkt(O.OracleLP.from_problem(P), x, y)["kkt"] <= 1.05e-4

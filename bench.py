@@ -545,7 +545,7 @@ def run_batch(args):
     acc = int(st2[:, 1].sum())
     kern = {}
     for kind, d in prof.items():
-        if not d["launches"] or kind == "kkt":
+        if not d["launches"] or kind in ("kkt", "gram"):
             continue
         bts = kernel_bytes(PK, 4, kind, M, d["launches"], 0, 0, 0) if kind != "mix" else None
         gbs = bts / (d["total_ms"] / 1e3) / 1e9 if bts else None

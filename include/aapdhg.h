@@ -216,7 +216,8 @@ aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta,
 /* Autotuning of the two PDHG half-step kernels (the SpMVs of eq. pdhg; the
  * paper has no counterpart).  They are compiled for AAPDHG_TASK_SHAPES task
  * shapes (shape 0: two SELL slices per warp task, 8 loads in flight per lane;
- * 1: one slice, 8 loads; 2: four slices, 8 loads), which sum every row in the
+ * 1: one slice, 8 loads; 2: four slices, 8 loads; 3: one slice, 16 loads;
+ * 4: two slices, 16 loads), which sum every row in the
  * same order, so the shape never changes a result.  By default the first
  * aapdhg_iterate times every shape on the handle's matrices and keeps the
  * fastest of each kernel.  aapdhg_autotune does that now and returns the
@@ -225,7 +226,7 @@ aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta,
  * run state.  aapdhg_set_task_shape fixes the two shapes (no tuning), or with
  * (-1, -1) re-enables tuning at the next iterate; other values give
  * AAPDHG_ERR_INVALID.                                                        */
-enum { AAPDHG_TASK_SHAPES = 3 };
+enum { AAPDHG_TASK_SHAPES = 5 };
 aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us);
 aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y);
 
@@ -383,7 +384,8 @@ aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6);
 aapdhg_status aapdhg_batch_get_status(aapdhg_batch_t h, int64_t *out6);
 
 /* CUDA-event timing of the batch kernels by kind: 0 half-step x, 1 half-step
- * y, 2 memory pass, 3 AA mix, 4 per-problem KKT; kind -1 gives in *launches
+ * y, 2 memory pass, 3 AA mix, 4 per-problem KKT, 5 per-problem Gram reduction
+ * and m x m work; kind -1 gives in *launches
  * the number of kernels launched since profiling was last (re)set.          */
 aapdhg_status aapdhg_batch_profile_kernels(aapdhg_batch_t h, int32_t enable);
 aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, int64_t *launches,

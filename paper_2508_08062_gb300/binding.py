@@ -17,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libaapdhg.so")
 
 OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NUMERIC, ERR_TIMEOUT, NOT_CONVERGED = range(7)
-TASK_SHAPES = 3
+TASK_SHAPES = 5
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NUMERIC",
                 5: "ERR_TIMEOUT", 6: "NOT_CONVERGED"}
 ROW_EQ, ROW_GE = 0, 1
@@ -361,7 +361,7 @@ class BatchSolver:
     norms, KKT rows, status rows) or as lists of per-problem (x, y).
     """
 
-    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "kkt")
+    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "kkt", "gram")
 
     def autotune(self):
         sx, sy = C.c_int32(), C.c_int32()

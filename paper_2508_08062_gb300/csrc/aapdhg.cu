@@ -244,8 +244,8 @@ struct aapdhg_s {
     // task shapes of the two half-step kernels (autotuned at the first iterate)
     int32_t shape_x = 0, shape_y = 0;
     bool tuned = false, autotune = true;
-    int32_t gridx[NSHAPE] = {1, 1, 1}, gridy[NSHAPE] = {1, 1, 1};
-    double tune_us[2 * NSHAPE] = {0, 0, 0, 0, 0, 0};
+    int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
+    double tune_us[2 * NSHAPE] = {};
     // primal weight update (off when pw_period = 0)
     int64_t pw_period = 0;
     double pw_theta = 0.5, pw_eps = 1e-10, pw_rho_min = 0.1, pw_alpha_dec = 0.1, pw_alpha_inc = 0.9;
@@ -433,9 +433,11 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     // launch (one in kkt_every) may run a short second wave
     int occ3 = 0;
     const int occx[NSHAPE] = {occupancy(k_xstep<V, false, 0>), occupancy(k_xstep<V, false, 1>),
-                              occupancy(k_xstep<V, false, 2>)};
+                              occupancy(k_xstep<V, false, 2>), occupancy(k_xstep<V, false, 3>),
+                              occupancy(k_xstep<V, false, 4>)};
     const int occy[NSHAPE] = {occupancy(k_ystep<V, false, 0>), occupancy(k_ystep<V, false, 1>),
-                              occupancy(k_ystep<V, false, 2>)};
+                              occupancy(k_ystep<V, false, 2>), occupancy(k_ystep<V, false, 3>),
+                              occupancy(k_ystep<V, false, 4>)};
     int gmax1 = 1, gmax2 = 1;
     for (int sh = 0; sh < NSHAPE; ++sh) {
         const int g = task_shape(sh).g;
@@ -573,6 +575,8 @@ template <typename V, bool KKT> void launch_x(aapdhg_t h, int shape, int mode) {
     Prob<V> &P = prob<V>(h);
     if (shape == 1) k_xstep<V, KKT, 1><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
     else if (shape == 2) k_xstep<V, KKT, 2><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 3) k_xstep<V, KKT, 3><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 4) k_xstep<V, KKT, 4><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
     else k_xstep<V, KKT, 0><<<P.grid1, BLOCK, 0, h->stream>>>(P, h->mp, mode);
 }
 
@@ -580,6 +584,8 @@ template <typename V, bool KKT> void launch_y(aapdhg_t h, int shape, int mode) {
     Prob<V> &P = prob<V>(h);
     if (shape == 1) k_ystep<V, KKT, 1><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
     else if (shape == 2) k_ystep<V, KKT, 2><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 3) k_ystep<V, KKT, 3><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    else if (shape == 4) k_ystep<V, KKT, 4><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
     else k_ystep<V, KKT, 0><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
 }
 

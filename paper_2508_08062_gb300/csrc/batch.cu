@@ -36,7 +36,7 @@ thread_local std::string g_batch_create_err;
 // done, error, init_done (the leading fields of DevState), 8-byte aligned.
 constexpr size_t HDR = (offsetof(DevState, want_aa) + 7) & ~(size_t)7;
 
-enum { BK_XSTEP = 0, BK_YSTEP = 1, BK_MEMORY = 2, BK_MIX = 3, BK_KKT = 4, BK_N = 5 };
+enum { BK_XSTEP = 0, BK_YSTEP = 1, BK_MEMORY = 2, BK_MIX = 3, BK_KKT = 4, BK_GRAM = 5, BK_N = 6 };
 
 }  // namespace
 
@@ -84,14 +84,14 @@ struct aapdhg_batch_s {
     // task shapes of the two half-step kernels (autotuned at the first iterate)
     int32_t shape_x = 0, shape_y = 0;
     bool tuned = false, autotune = true;
-    int32_t gridx[NSHAPE] = {1, 1, 1}, gridy[NSHAPE] = {1, 1, 1};
-    double tune_us[2 * NSHAPE] = {0, 0, 0, 0, 0, 0};
+    int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
+    double tune_us[2 * NSHAPE] = {};
     // instrumentation
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;
-    double prof_ms[BK_N] = {0, 0, 0, 0, 0};
-    int64_t prof_n[BK_N] = {0, 0, 0, 0, 0};
+    double prof_ms[BK_N] = {0, 0, 0, 0, 0, 0};
+    int64_t prof_n[BK_N] = {0, 0, 0, 0, 0, 0};
     int64_t launches = 0;
 };
 
@@ -237,9 +237,11 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     if (!P.UP || !P.dh || !P.g) ok = false;
     // grids per task shape for the common (non-KKT) variants: all their blocks resident
     const int occx[NSHAPE] = {boccupancy(k_xstep_b<V, false, 0>), boccupancy(k_xstep_b<V, false, 1>),
-                              boccupancy(k_xstep_b<V, false, 2>)};
+                              boccupancy(k_xstep_b<V, false, 2>), boccupancy(k_xstep_b<V, false, 3>),
+                              boccupancy(k_xstep_b<V, false, 4>)};
     const int occy[NSHAPE] = {boccupancy(k_ystep_b<V, false, 0>), boccupancy(k_ystep_b<V, false, 1>),
-                              boccupancy(k_ystep_b<V, false, 2>)};
+                              boccupancy(k_ystep_b<V, false, 2>), boccupancy(k_ystep_b<V, false, 3>),
+                              boccupancy(k_ystep_b<V, false, 4>)};
     for (int sh = 0; sh < NSHAPE; ++sh) {
         const int g = task_shape(sh).g;
         h->gridx[sh] = bgrid(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
@@ -338,6 +340,9 @@ template <typename V, int MC> void blaunch_memory_mix(bh_t h, int cur) {
     bmark_begin(h, BK_MEMORY);
     k_memory_b<V, MC><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
     bmark_end(h);
+    bmark_begin(h, BK_GRAM);
+    k_gram_b<MC><<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, h->prec == AAPDHG_FP64 ? 1 : 0, h->mp);
+    bmark_end(h);
     if (M > 0) {
         bmark_begin(h, BK_MIX);
         k_mix_b<V, MC><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
@@ -350,6 +355,8 @@ template <typename V, bool KKT> void blaunch_x(bh_t h, int shape, int cur, int m
     BatchView<V> &B = bview<V>(h);
     if (shape == 1) k_xstep_b<V, KKT, 1><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
     else if (shape == 2) k_xstep_b<V, KKT, 2><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 3) k_xstep_b<V, KKT, 3><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 4) k_xstep_b<V, KKT, 4><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
     else k_xstep_b<V, KKT, 0><<<P.grid1, BLOCK, 0, h->stream>>>(P, B, cur, mode);
 }
 
@@ -358,6 +365,8 @@ template <typename V, bool KKT> void blaunch_y(bh_t h, int shape, int cur, int m
     BatchView<V> &B = bview<V>(h);
     if (shape == 1) k_ystep_b<V, KKT, 1><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
     else if (shape == 2) k_ystep_b<V, KKT, 2><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 3) k_ystep_b<V, KKT, 3><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
+    else if (shape == 4) k_ystep_b<V, KKT, 4><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
     else k_ystep_b<V, KKT, 0><<<P.grid2, BLOCK, 0, h->stream>>>(P, B, cur, mode);
 }
 
@@ -444,7 +453,7 @@ template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
 int launches_per_iter(bh_t h, int64_t g) {
     const bool kkt = h->kkt_every > 0 && g >= 1 && (g - 1) % h->kkt_every == 0;
     const bool mix = h->mp.method != 0 && h->mp.mem > 0;
-    return 3 + (kkt ? 1 : 0) + (mix ? 1 : 0);
+    return 4 + (kkt ? 1 : 0) + (mix ? 1 : 0);
 }
 
 template <typename V> bool blaunch_chunk_graph(bh_t h, int64_t g0) {

@@ -25,9 +25,9 @@
 //   k_kkt_b                per-problem KKT of u^k (Remark on termination) and
 //                          the stop test (KKT iterations only);
 //   k_memory_b             per chunk of a problem's elements: the memory pass
-//                          plus ||g^k||^2; the block whose chunk of a problem
-//                          arrives last reduces that problem's partials and
-//                          runs its safeguard and m x m work;
+//                          plus ||g^k||^2 (chunk partial sums);
+//   k_gram_b               per problem (one warp): the fixed-order reduction of
+//                          its chunk partials, its safeguard and m x m work;
 //   k_mix_b                the AA mix of the problems whose step was accepted.
 #pragma once
 #include "anderson.cuh"
@@ -245,9 +245,11 @@ __global__ void __launch_bounds__(BLOCK) k_kkt_b(BatchView<V> B, double tol, int
 }
 
 // --------------------------------------------------------------------------
-// Memory pass, ||g^k|| and the per-problem m x m work.  Grid: one block per
-// chunk.  A problem that stopped at this iteration's KKT test (done == 1) has
-// its iterate copied into both components instead (done becomes 2).
+// Memory pass and ||g^k||^2, per chunk (one block each): a pure stream that
+// writes the chunk's partial sums.  A problem that stopped at this
+// iteration's KKT test (done == 1) has its iterate copied into both
+// components instead.  The per-problem reduction and m x m work follow in
+// k_gram_b, so no block holds its SM slot through a solve.
 // --------------------------------------------------------------------------
 template <typename V, int MC>
 __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, MethodParams mp, int cur) {
@@ -255,9 +257,8 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     typedef typename Vec2<V>::T V2;
     const int4 ch = B.chunk[blockIdx.x];
     const int p = ch.x;
-    DevState *st = B.stb + p;
+    const DevState *st = B.stb + p;
     if (st->error || st->done == 2) return;
-    const int c0 = B.pchunk0[p], c1 = B.pchunk0[p + 1];
     const int64_t e0 = ch.y, e1 = (int64_t)ch.y + ch.z;
     if (st->done) {
         for (int64_t e = e0 + threadIdx.x; e < e1; e += BLOCK) {
@@ -265,29 +266,27 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
             if (cur) pr.x = pr.y; else pr.y = pr.x;
             P.UP[e] = pr;
         }
-        if (last_chunk(B.pcnt + p, c1 - c0) && threadIdx.x == 0) st->done = 2;
         return;
     }
     const bool init = !st->init_done;
     const int M = (mp.method == 0) ? 0 : mp.mem;
-    __shared__ int s_old[NSLOT];
+    if (M == 0) return;
     __shared__ int64_t s_off[NSLOT];
     __shared__ int s_nold, s_new, s_prev_acc;
     __shared__ double sh[WARPS * (MC + 4)];
     if (threadIdx.x == 0) {
-        int t = 0;
-        if (!init) {
-            const int cnt = st->count;
-            const int drop = (M > 0 && cnt == M) ? 1 : 0;
-            for (int i = drop; i < cnt; ++i) s_old[t++] = st->list[i];
-        }
-        s_nold = t;
+        const int cnt = init ? 0 : st->count;
+        const int drop = (cnt == M) ? 1 : 0;
+        s_nold = cnt - drop;
         s_new = init ? 0 : st->free_slot;
         s_prev_acc = init ? 0 : st->accept;
     }
     __syncthreads();
-    if (threadIdx.x < NSLOT)
-        s_off[threadIdx.x] = (int64_t)s_old[threadIdx.x < s_nold ? threadIdx.x : 0] * P.Npad;
+    if (threadIdx.x < NSLOT) {
+        const int t = threadIdx.x;
+        const int drop = (!init && st->count == M) ? 1 : 0;
+        s_off[t] = (int64_t)(t < s_nold ? st->list[t + drop] : 0) * P.Npad;
+    }
     __syncthreads();
     const int nold = s_nold, sn = s_new;
     const bool prev_acc = s_prev_acc != 0;
@@ -295,7 +294,7 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2; MC+3: ||g||^2
     Acc<V> acc[MC + 4];
     const int64_t stride = (int64_t)BLOCK * W;
-    if (M > 0 && init) {
+    if (init) {
         // g^0 = u^1 - u^0 (u^1 = T u^0 was just written into the other component)
         const V *UPs = reinterpret_cast<const V *>(P.UP);
         for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride) {
@@ -311,43 +310,85 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
             }
             aap::st<V, W>(P.g + e, gk);
         }
-    } else if (M > 0) {
+    } else {
         V *DGn = P.DG + (int64_t)sn * P.Npad;
         V *Wn = P.W + (int64_t)sn * P.Npad;
         const V beta = (V)mp.beta;
         for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride)
             memory_elems<V, MC, W, true>(P, e, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
     }
-    {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int s = 0; s < MC + 4; ++s) {
-            if (s < nold || s >= MC) {
-                acc[s].warp_allreduce();
-                if (lane == 0) sh[warp * (MC + 4) + s] = acc[s].value();
-            }
+    for (int k = 0; k < MC + 4; ++k) {
+        if (k < nold || k >= MC) {
+            acc[k].warp_allreduce();
+            if (lane == 0) sh[warp * (MC + 4) + k] = acc[k].value();
         }
-        __syncthreads();
-        for (int s = threadIdx.x; s < MC + 4; s += BLOCK) {
-            if (s < nold || s >= MC) {
-                double v = 0.0;
-                for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 4) + s];
-                B.cpart[(int64_t)blockIdx.x * NBV + (s < MC ? s : MAXM + (s - MC))] = v;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < MC + 4; k += BLOCK) {
+        if (k < nold || k >= MC) {
+            double v = 0.0;
+            for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 4) + k];
+            B.cpart[(int64_t)blockIdx.x * NBV + (k < MC ? k : MAXM + (k - MC))] = v;
+        }
+    }
+}
+
+// --------------------------------------------------------------------------
+// Per-problem reduction of the memory pass's chunk partials (fixed order),
+// the safeguard of Alg. 2 / Alg. 3 and the m x m work (the single-LP code).
+// Grid: one warp per problem.
+// --------------------------------------------------------------------------
+template <int MC>
+__global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<double> Bd, int fp64,
+                                               MethodParams mp) {
+    const int p = blockIdx.x;
+    DevState *st = fp64 ? Bd.stb + p : Bf.stb + p;
+    const int32_t *pchunk0 = fp64 ? Bd.pchunk0 : Bf.pchunk0;
+    const double *cpart = fp64 ? Bd.cpart : Bf.cpart;
+    const int lane = threadIdx.x;
+    if (st->error || st->done == 2) return;
+    if (st->done) {                       // stopped at this iteration's KKT test: now frozen
+        if (lane == 0) st->done = 2;
+        return;
+    }
+    const bool init = !st->init_done;
+    const int M = (mp.method == 0) ? 0 : mp.mem;
+    __shared__ int s_old[NSLOT];
+    __shared__ double red[MC + 3];
+    __shared__ double gsq;
+    __shared__ SolveSmem sm;
+    const int cnt = init ? 0 : st->count;
+    const int drop = (M > 0 && cnt == M) ? 1 : 0;
+    const int nold = cnt - drop;
+    const int sn = init ? 0 : st->free_slot;
+    for (int t = lane; t < nold; t += 32) s_old[t] = st->list[t + drop];
+    // fixed-order sums over the problem's chunks: Gram row, ||dg||^2, <dg,g>,
+    // ||du||^2, ||g||^2
+    const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
+    if (M > 0) {
+        // every lane loads all columns of its chunks at once (independent
+        // loads), then one shuffle tree per column
+        double v[MC + 4];
+#pragma unroll
+        for (int k = 0; k < MC + 4; ++k) v[k] = 0.0;
+        for (int c = c0 + lane; c < c1; c += 32)
+#pragma unroll
+            for (int k = 0; k < MC + 4; ++k)
+                if (k < nold || k >= MC) v[k] += __ldcg(cpart + (int64_t)c * NBV + (k < MC ? k : MAXM + (k - MC)));
+#pragma unroll
+        for (int k = 0; k < MC + 4; ++k) {
+#pragma unroll
+            for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+            if (lane == 0 && (k < nold || k >= MC)) {
+                if (k < MC + 3) red[k] = v[k];
+                else gsq = v[k];
             }
         }
     }
-    if (!last_chunk(B.pcnt + p, c1 - c0)) return;
-
-    // ---- this problem's reduction and m x m work (one block) --------------
-    __shared__ double redb[NBV];
-    __shared__ double red[MC + 3];
-    __shared__ SolveSmem sm;
-    unsigned long long active = 0xFull << MAXM;
-    for (int t = 0; t < nold; ++t) active |= 1ull << t;
-    if (M > 0) reduce_chunks(B.cpart, c0, c1, NBV, redb, active);
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
-    const double gn = M > 0 ? sqrt(redb[MAXM + 3]) : 0.0;
+    __syncwarp();
+    const double gn = M > 0 ? sqrt(gsq) : 0.0;
     if (init) {
         if (lane == 0) {
             if (!isfinite(gn)) st->error = 1;
@@ -366,12 +407,6 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     if (!isfinite(gn)) {
         if (lane == 0) st->error = 1;
         return;
-    }
-    for (int t = lane; t < nold; t += 32) red[t] = redb[t];
-    if (lane == 0 && M > 0) {
-        red[MC] = redb[MAXM];
-        red[MC + 1] = redb[MAXM + 1];
-        red[MC + 2] = redb[MAXM + 2];
     }
     bool want = false;
     if (mp.method != 0 && M > 0)

@@ -22,9 +22,13 @@ constexpr int SLICES_PER_TASK = 2;  // SELL slices one warp reads in lockstep
 struct TaskShape {
     int g, ld;
 };
-constexpr int NSHAPE = 3;
+constexpr int NSHAPE = 5;
 __host__ __device__ constexpr TaskShape task_shape(int s) {
-    return s == 1 ? TaskShape{1, 8} : (s == 2 ? TaskShape{4, 8} : TaskShape{SLICES_PER_TASK, LOADS});
+    return s == 1 ? TaskShape{1, 8}
+         : s == 2 ? TaskShape{4, 8}
+         : s == 3 ? TaskShape{1, 16}
+         : s == 4 ? TaskShape{2, 16}
+                  : TaskShape{SLICES_PER_TASK, LOADS};
 }
 
 // ---------------------------------------------------------------------------

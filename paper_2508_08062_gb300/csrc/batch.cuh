@@ -368,23 +368,16 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     // ||du||^2, ||g||^2
     const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
     if (M > 0) {
-        // every lane loads all columns of its chunks at once (independent
-        // loads), then one shuffle tree per column
-        double v[MC + 4];
-#pragma unroll
-        for (int k = 0; k < MC + 4; ++k) v[k] = 0.0;
-        for (int c = c0 + lane; c < c1; c += 32)
-#pragma unroll
-            for (int k = 0; k < MC + 4; ++k)
-                if (k < nold || k >= MC) v[k] += __ldcg(cpart + (int64_t)c * NBV + (k < MC ? k : MAXM + (k - MC)));
-#pragma unroll
-        for (int k = 0; k < MC + 4; ++k) {
-#pragma unroll
-            for (int o = 16; o; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
-            if (lane == 0 && (k < nold || k >= MC)) {
-                if (k < MC + 3) red[k] = v[k];
-                else gsq = v[k];
-            }
+        // lane k sums column k over the problem's chunks in chunk order: one
+        // FP64 add per chunk and lane, no cross-lane tree (FP64 issue is the
+        // scarce resource here)
+        for (int k = lane; k < MC + 4; k += 32) {
+            if (!(k < nold || k >= MC)) continue;
+            const int col = k < MC ? k : MAXM + (k - MC);
+            double v = 0.0;
+            for (int c = c0; c < c1; ++c) v += __ldcg(cpart + (int64_t)c * NBV + col);
+            if (k < MC + 3) red[k] = v;
+            else gsq = v;
         }
     }
     __syncwarp();
@@ -408,10 +401,10 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
         if (lane == 0) st->error = 1;
         return;
     }
-    bool want = false;
-    if (mp.method != 0 && M > 0)
-        want = gn <= mp.D * st->g0 * pow((double)st->n_aa / mp.c_div + 1.0, -(1.0 + mp.eps));
-    if (lane == 0) {
+    if (lane == 0) {                      // the safeguard on one lane
+        bool want = false;
+        if (mp.method != 0 && M > 0)
+            want = gn <= mp.D * st->g0 * safeguard_factor(st, mp.c_div, mp.eps);
         st->gnorm = gn;
         st->want_aa = want ? 1 : 0;
     }

@@ -114,6 +114,8 @@ struct DevState {
     double g0;             // ||g^0||
     double gnorm;          // ||g^k||
     double gnorm_prev;     // ||g^{k-1}||
+    int64_t thr_key;       // n_aa + 1 when thr_fac holds (i/c_div + 1)^-(1+eps) for i = n_aa
+    double thr_fac;        // cached safeguard factor (FP64 pow is slow on this part)
     int32_t restart;       // primal weight update: this iteration restarts the memory
     double kkt[6];         // r_p, r_d, r_g, KKT, c'x, dual objective at u^k
     int32_t kkt_valid;
@@ -122,6 +124,16 @@ struct DevState {
     uint32_t cnt_norm;     // last-block counter of the norm kernels
     double scratch[8];
 };
+
+// Safeguard factor (i^k / c_div + 1)^-(1+eps) of Alg. 2 (reading R3), cached
+// per value of i^k = n_aa: it changes only when an AA step is accepted.
+__device__ __forceinline__ double safeguard_factor(DevState *st, double c_div, double eps) {
+    if (st->thr_key != st->n_aa + 1) {
+        st->thr_fac = pow((double)st->n_aa / c_div + 1.0, -(1.0 + eps));
+        st->thr_key = st->n_aa + 1;
+    }
+    return st->thr_fac;
+}
 
 // Method parameters (by value into the kernels).
 struct MethodParams {
@@ -272,7 +284,9 @@ __device__ __forceinline__ bool last_block(uint32_t *cnt) {
 
 // Fixed-order FP64 sums over `nb` blocks of columns [0, NC) of part[nb][stride]
 // in one pass (one load round, warp shuffles, one shared-memory stage), by one
-// block; out[k] valid in every thread on return.
+// block; out[k] is valid in thread 0 on return (the only thread that needs
+// it: FP64 issue is scarce on this part, so the other warps skip the last
+// stage).
 template <int NC>
 __device__ __forceinline__ void block_sum_columns(const double *part, int nb, int stride,
                                                   double (&out)[NC], double *sh) {
@@ -290,11 +304,13 @@ __device__ __forceinline__ void block_sum_columns(const double *part, int nb, in
         if (lane == 0) sh[warp * NC + k] = s[k];
     }
     __syncthreads();
+    if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < NC; ++k) {
-        double t = 0.0;
-        for (int w = 0; w < nw; ++w) t += sh[w * NC + k];
-        out[k] = t;
+        for (int k = 0; k < NC; ++k) {
+            double t = 0.0;
+            for (int w = 0; w < nw; ++w) t += sh[w * NC + k];
+            out[k] = t;
+        }
     }
     __syncthreads();
 }

@@ -238,8 +238,13 @@ __global__ void __launch_bounds__(BLOCK) k_xstep(Prob<V> P, MethodParams mp, int
         const int64_t t = vb * WARPS + warp;
         if (t < ntask) run_task<V, 1, ts.g, ts.ld>(P.KT, t, gat, epi);
     }
-    Acc<V> a4[4] = {g2, dres2, lam, cx};
-    block_reduce_store<V, 4>(a4, sh, P.part1 + (int64_t)blockIdx.x * 4);
+    if constexpr (KKT) {
+        Acc<V> a4[4] = {g2, dres2, lam, cx};
+        block_reduce_store<V, 4>(a4, sh, P.part1 + (int64_t)blockIdx.x * 4);
+    } else {                                   // only ||g||^2 is used without KKT terms
+        Acc<V> a1[1] = {g2};
+        block_reduce_store<V, 1>(a1, sh, P.part1 + (int64_t)blockIdx.x * 4);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -293,12 +298,20 @@ template <typename V, bool KKT> struct EpiY {
 template <typename V>
 __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, bool kkt) {
     __shared__ double sh[WARPS * 4];
-    double a1[4], a2[3];
-    block_sum_columns<4>(P.part1, P.grid1, 4, a1, sh);
-    block_sum_columns<3>(P.part2, P.grid2, 3, a2, sh);
+    double a1[4] = {0, 0, 0, 0}, a2[3] = {0, 0, 0};
+    if (kkt) {
+        block_sum_columns<4>(P.part1, P.grid1, 4, a1, sh);
+        block_sum_columns<3>(P.part2, P.grid2, 3, a2, sh);
+    } else {                                   // only ||g||^2 without KKT terms
+        double b1[1], b2[1];
+        block_sum_columns<1>(P.part1, P.grid1, 4, b1, sh);
+        block_sum_columns<1>(P.part2, P.grid2, 3, b2, sh);
+        a1[0] = b1[0];
+        a2[0] = b2[0];
+    }
+    if (threadIdx.x != 0) return;
     const double g2 = a1[0] + a2[0];
     const double dres2 = a1[1], lam = a1[2], cx = a1[3], pres2 = a2[1], qy = a2[2];
-    if (threadIdx.x != 0) return;
     DevState *st = P.st;
     const double gn = sqrt(g2);
     double out[6] = {0, 0, 0, 0, 0, 0};
@@ -330,7 +343,7 @@ __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, b
     }
     bool want = false;
     if (mp.method != 0 && mp.mem > 0) {
-        const double thr = mp.D * st->g0 * pow((double)st->n_aa / mp.c_div + 1.0, -(1.0 + mp.eps));
+        const double thr = mp.D * st->g0 * safeguard_factor(st, mp.c_div, mp.eps);
         want = gn <= thr;
     }
     st->want_aa = want ? 1 : 0;
@@ -352,8 +365,13 @@ __global__ void __launch_bounds__(BLOCK) k_ystep(Prob<V> P, MethodParams mp, int
         if (t < ntask) run_task<V, KKT ? 2 : 1, ts.g, ts.ld>(P.K, t, gat, epi);
     }
     if (mode == MODE_TUNE) return;
-    Acc<V> a3[3] = {g2, pres2, qy};
-    block_reduce_store<V, 3>(a3, sh, P.part2 + (int64_t)blockIdx.x * 3);
+    if constexpr (KKT) {
+        Acc<V> a3[3] = {g2, pres2, qy};
+        block_reduce_store<V, 3>(a3, sh, P.part2 + (int64_t)blockIdx.x * 3);
+    } else {
+        Acc<V> a1[1] = {g2};
+        block_reduce_store<V, 1>(a1, sh, P.part2 + (int64_t)blockIdx.x * 3);
+    }
     if (last_block(&P.st->cnt_spmv)) finalize_T<V>(P, mp, mode, KKT);
 }
 

@@ -72,6 +72,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device="cuda"):
+    """The largest of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_rank, t_max_ms):
+    """Units of all ranks per second of the slowest rank (replicas: weak scaling)."""
+    return world * units_per_rank / (t_max_ms / 1e3)
+
+
 def make_problem(workload, rank, scale=1.0):
     import lpgen
     seed = lpgen.SEED_BASE + {"tiny": 1, "medium": 2, "large": 3}[workload] + 1000 * rank
@@ -222,12 +238,8 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     launches = s.launch_count() - l0
     c1 = s.counters()
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps / (t_max / 1e3)
+    t_max = max_over_ranks(ms, world)
+    value = whole_job_rate(world, args.steps, t_max)
 
     # per-kernel CUDA-event pass (same loop, instrumented), for the roofline
     s.profile_kernels(True)
@@ -360,11 +372,7 @@ def run_ours(args):
         s2.iterate(args.steps, tol=0.0, kkt_every=kkt_every)
         x, y = s2.get_iterate()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
     polls = (args.steps + 63) // 64 + 2
     e2e = {"value": world * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": problem_bytes(P) / args.steps,
@@ -506,12 +514,8 @@ def run_batch(args):
     launches = b.launch_count() - l0
     st = b.status()
     solved = int(st[:, 4].sum())
-    t_max = ms
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * solved / (t_max / 1e3)
+    t_max = max_over_ranks(ms, world)
+    value = whole_job_rate(world, solved, t_max)
     kk = b.get_kkt()
 
     # throughput with every member active (tol = 0) and the roofline

@@ -29,43 +29,53 @@ namespace aap {
 // (row-major, leading dimension NSLOT).
 // ---------------------------------------------------------------------------
 
-// Cholesky A = L L' in place (lower triangle).  Returns false when a pivot is
-// not positive (or not finite).
-static __device__ bool warp_cholesky(double *A, int k) {
+// FP64 issue is scarce on this part (a warp-wide FP64 instruction occupies the
+// pipe for many cycles whatever the active lanes), so the dense routines are
+// written to issue few FP64 instructions: right-looking Cholesky with one
+// reciprocal per pivot and the trailing update spread over the lanes, and
+// column-oriented triangular solves.
+
+// Cholesky A = L L' in place (lower triangle), rd[j] = 1 / L[j][j].  Returns
+// false when a pivot is not positive (or not finite).
+static __device__ bool warp_cholesky(double *A, double *rd, int k) {
     const int lane = threadIdx.x & 31;
-    bool ok = true;
     for (int j = 0; j < k; ++j) {
-        // pivot (lane 0), then column j below the pivot (lane i handles row i)
-        if (lane == 0) {
-            double d = A[j * NSLOT + j];
-            for (int p = 0; p < j; ++p) d -= A[j * NSLOT + p] * A[j * NSLOT + p];
-            A[j * NSLOT + j] = (d > 0.0 && isfinite(d)) ? sqrt(d) : -1.0;
-        }
+        const double d = A[j * NSLOT + j];
+        if (!(d > 0.0 && isfinite(d))) return false;      // uniform: every lane reads d
+        const double piv = sqrt(d), r = 1.0 / piv;
         __syncwarp();
-        const double piv = A[j * NSLOT + j];
-        if (!(piv > 0.0)) { ok = false; break; }
+        if (lane == 0) {
+            A[j * NSLOT + j] = piv;
+            rd[j] = r;
+        }
+        for (int i = j + 1 + lane; i < k; i += 32) A[i * NSLOT + j] *= r;
+        __syncwarp();
+        // trailing update of the lower triangle, row i per lane
         for (int i = j + 1 + lane; i < k; i += 32) {
-            double s = A[i * NSLOT + j];
-            for (int p = 0; p < j; ++p) s -= A[i * NSLOT + p] * A[j * NSLOT + p];
-            A[i * NSLOT + j] = s / piv;
+            const double lij = A[i * NSLOT + j];
+            for (int l = j + 1; l <= i; ++l) A[i * NSLOT + l] -= lij * A[l * NSLOT + j];
         }
         __syncwarp();
     }
-    return ok;
+    return true;
 }
 
-// Solve L L' x = b (b overwritten by x), lane 0.
-static __device__ void chol_solve_lane0(const double *L, double *b, int k) {
-    if ((threadIdx.x & 31) != 0) return;
-    for (int i = 0; i < k; ++i) {
-        double s = b[i];
-        for (int p = 0; p < i; ++p) s -= L[i * NSLOT + p] * b[p];
-        b[i] = s / L[i * NSLOT + i];
+// Solve L L' x = b (b overwritten by x), column by column; rd = 1 / diag(L).
+static __device__ void warp_chol_solve(const double *L, const double *rd, double *b, int k) {
+    const int lane = threadIdx.x & 31;
+    for (int j = 0; j < k; ++j) {                       // L y = b
+        const double yj = b[j] * rd[j];
+        __syncwarp();
+        if (lane == 0) b[j] = yj;
+        for (int i = j + 1 + lane; i < k; i += 32) b[i] -= L[i * NSLOT + j] * yj;
+        __syncwarp();
     }
-    for (int i = k - 1; i >= 0; --i) {
-        double s = b[i];
-        for (int p = i + 1; p < k; ++p) s -= L[p * NSLOT + i] * b[p];
-        b[i] = s / L[i * NSLOT + i];
+    for (int j = k - 1; j >= 0; --j) {                  // L' x = y
+        const double xj = b[j] * rd[j];
+        __syncwarp();
+        if (lane == 0) b[j] = xj;
+        for (int i = lane; i < j; i += 32) b[i] -= L[j * NSLOT + i] * xj;
+        __syncwarp();
     }
 }
 
@@ -73,6 +83,7 @@ static __device__ void chol_solve_lane0(const double *L, double *b, int k) {
 struct SolveSmem {
     double A[NSLOT * NSLOT];
     double b[NSLOT];
+    double rd[NSLOT];
     double sig[NSLOT];
     double bnd[NSLOT];
     double pw[NSLOT + 1];
@@ -179,10 +190,10 @@ static __device__ bool gram_solve(DevState *st, const int *cols, int k, double e
     }
     for (int t = lane; t < k; t += 32) sm.b[t] = st->rhs[cols[t]];
     __syncwarp();
-    const bool ok = warp_cholesky(sm.A, k);
+    const bool ok = warp_cholesky(sm.A, sm.rd, k);
     __syncwarp();
     if (ok) {
-        chol_solve_lane0(sm.A, sm.b, k);
+        warp_chol_solve(sm.A, sm.rd, sm.b, k);
         __syncwarp();
         bool fin = true;
         for (int t = 0; t < k; ++t) fin = fin && isfinite(sm.b[t]);

@@ -60,6 +60,7 @@ struct aapdhg_batch_s {
     std::vector<double> lo_x, hi_x, x0, y0;        // caller order, concatenated
     std::vector<int8_t> sense;
     std::vector<double> tau, sigma;
+    std::vector<float> tau_f, sigma_f;             // the steps rounded once (mixed precision)
     int64_t n_tot = 0, m_tot = 0, N = 0, Npad = 0;
 
     Prob<float> pf{};
@@ -272,11 +273,13 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     B.pnorm = bput(h, pnorm, &ok);
     B.tau = (const double *)bdev_alloc(h, sizeof(double) * h->nprob);
     B.sigma = (const double *)bdev_alloc(h, sizeof(double) * h->nprob);
+    B.tau_v = (const V *)bdev_alloc(h, sizeof(V) * h->nprob);
+    B.sigma_v = (const V *)bdev_alloc(h, sizeof(V) * h->nprob);
     B.stb = (DevState *)bdev_alloc(h, sizeof(DevState) * h->nprob);
     B.kterm = (V *)bdev_alloc(h, sizeof(V) * (3 * h->n_tot + 2 * h->m_tot));
     B.cpart = (double *)bdev_alloc(h, sizeof(double) * NBV * B.nchunk);
     B.pcnt = (uint32_t *)bdev_alloc(h, sizeof(uint32_t) * h->nprob);
-    if (!B.tau || !B.sigma || !B.stb || !B.kterm || !B.cpart || !B.pcnt) ok = false;
+    if (!B.tau || !B.sigma || !B.tau_v || !B.sigma_v || !B.stb || !B.kterm || !B.cpart || !B.pcnt) ok = false;
     if (!ok) return bfail(h, AAPDHG_ERR_OOM, "device allocation or copy failed during create");
     h->stb = B.stb;
     BCK(h, cudaMemsetAsync(B.stb, 0, sizeof(DevState) * h->nprob, h->stream));
@@ -885,6 +888,15 @@ aapdhg_status aapdhg_batch_set_steps(aapdhg_batch_t h, const double *tau, const 
     const double *ds = h->prec == AAPDHG_FP64 ? h->bd.sigma : h->bf.sigma;
     BCK(h, cudaMemcpyAsync(const_cast<double *>(dt), tau, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
     BCK(h, cudaMemcpyAsync(const_cast<double *>(ds), sigma, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+    if (h->prec == AAPDHG_FP64) {
+        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.tau_v), tau, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.sigma_v), sigma, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+    } else {
+        h->tau_f.assign(tau, tau + h->nprob);
+        h->sigma_f.assign(sigma, sigma + h->nprob);
+        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.tau_v), h->tau_f.data(), 4 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.sigma_v), h->sigma_f.data(), 4 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
+    }
     bdrop_graphs(h);
     return breset_any(h);
 }

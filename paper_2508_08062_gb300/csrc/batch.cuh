@@ -43,6 +43,7 @@ template <typename V> struct BatchView {
     int32_t nprob;
     int64_t n_tot, m_tot;             // variables and constraints of all problems (padded)
     const double *tau, *sigma;        // per problem
+    const V *tau_v, *sigma_v;         // the same in the iterate precision (no per-row conversion)
     DevState *stb;                    // per problem
     V *kterm;                         // KKT terms: 3 arrays over variables, then 2 over constraints
     int32_t nchunk;
@@ -70,7 +71,7 @@ template <typename V, bool KKT> struct EpiXB {
         return mode != MODE_EVAL && stopped(B.stb + p);
     }
     __device__ __forceinline__ Pre pre(int j, int p) const {
-        return Pre{P.UP[j], __ldg(P.c + j), __ldg(P.lo + j), __ldg(P.hi + j), (V)__ldg(B.tau + p),
+        return Pre{P.UP[j], __ldg(P.c + j), __ldg(P.lo + j), __ldg(P.hi + j), __ldg(B.tau_v + p),
                    (int)stopped(B.stb + p)};
     }
     __device__ __forceinline__ void operator()(int j, const Pre &in, const V (&s)[1]) {
@@ -115,7 +116,7 @@ template <typename V, bool KKT> struct EpiYB {
         return mode != MODE_EVAL && stopped(B.stb + p);
     }
     __device__ __forceinline__ Pre pre(int i, int p) const {
-        return Pre{P.UP[P.n + i], __ldg(P.q + i), __ldg(P.lo + P.n + i), (V)__ldg(B.sigma + p),
+        return Pre{P.UP[P.n + i], __ldg(P.q + i), __ldg(P.lo + P.n + i), __ldg(B.sigma_v + p),
                    (int)stopped(B.stb + p)};
     }
     __device__ __forceinline__ void operator()(int i, const Pre &in, const V (&t)[KKT ? 2 : 1]) {

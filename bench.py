@@ -351,6 +351,7 @@ def run_ours(args):
                             "two passes of 5 + %d iterations from u^0" % n_ae}
 
     s.close()
+    libspmv = library_spmv(P) if args.library_spmv else None
 
     # end to end through the public API from pinned host buffers
     import lpgen
@@ -409,12 +410,58 @@ def run_ours(args):
             "plain_pdhg": {"iters_per_s": args.steps / (pd_ms / 1e3), "ms_per_iter": pd_ms / args.steps},
             "aa_every_step": aa_every,
             "kkt_after_run": kk["kkt"],
+            "library_spmv": libspmv,
             "time_to_1e-4": ttt,
             "p99_latency": None,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def library_spmv(P, reps=20):
+    """Context for the half-steps: a plain FP32 CSR SpMV (K v and K' w) by the
+    vendor library (torch.sparse CSR with int32 indices, which calls cuSPARSE)
+    on the same matrix, in the caller's order and with rows and columns sorted
+    by degree (the order the half-steps use).  Reports the average time per
+    product over `reps` CUDA-event-timed launches after 3 warm-up launches and
+    the plain SpMV's bytes (values, indices, row pointers, x once, y) per
+    second.  Not part of the solver: the fused half-steps also apply the prox
+    operators and accumulate ||g||."""
+    import scipy.sparse as sp
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    K = sp.csr_matrix((P.val.astype(np.float32), P.col_idx, P.row_ptr), shape=(P.m, P.n))
+    deg_r = np.diff(P.row_ptr)
+    deg_c = np.bincount(P.col_idx, minlength=P.n)
+    pr = np.argsort(-deg_r, kind="stable")
+    pc = np.argsort(-deg_c, kind="stable")
+    Ks = K[pr][:, pc].tocsr()
+    Ks.sort_indices()
+    out = {"library": "cuSPARSE SpMV via torch.sparse_csr_tensor (FP32 values, int32 indices)",
+           "reps": reps}
+    for order, A in (("caller", K), ("degree_sorted", Ks)):
+        for name, M in (("K_v", A), ("KT_w", A.T.tocsr())):
+            M.sort_indices()
+            t = torch.sparse_csr_tensor(
+                torch.from_numpy(M.indptr.astype(np.int32)), torch.from_numpy(M.indices.astype(np.int32)),
+                torch.from_numpy(M.data), size=M.shape, check_invariants=True).to(dev)
+            v = torch.randn(M.shape[1], device=dev)
+            for _ in range(3):
+                r = torch.mv(t, v)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(reps):
+                r = torch.mv(t, v)
+            e1.record()
+            torch.cuda.synchronize()
+            us = 1e3 * e0.elapsed_time(e1) / reps
+            b = 8 * M.nnz + 4 * (M.shape[0] + 1) + 4 * M.shape[1] + 4 * M.shape[0]
+            out[f"{order}_{name}"] = {"avg_us": us, "gbs": b / us / 1e3}
+            del t, v, r
+    torch.cuda.empty_cache()
+    return out
 
 
 KERNEL_FILES = {"xstep": ("common.cuh", "spmv.cuh"), "ystep": ("common.cuh", "spmv.cuh"),
@@ -909,6 +956,8 @@ def main():
     ap.add_argument("--max-cohorts", type=int, default=4)
     ap.add_argument("--cohort-size", type=int, default=64)
     ap.add_argument("--serve-max-iters", type=int, default=100000)
+    ap.add_argument("--library-spmv", action="store_true",
+                    help="single-LP workloads: also time the vendor library's plain SpMV on K, K'")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="shrink the workload's m, n, nnz (profiling captures only)")
     args = ap.parse_args()

@@ -264,14 +264,7 @@ def run_ours(args):
     for kind in kern:
         kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
     dom = max(kern, key=lambda k: prof[k]["total_ms"])
-    traffic = None
-    try:
-        tf = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-        ent = tf.get(args.workload, {}).get(dom) if args.scale == 1.0 else None
-        if ent and ent.get("kernel_sources") == kernel_source_hash(dom):
-            traffic = ent["dram_bytes_per_launch"]
-    except Exception:
-        pass
+    traffic = committed_traffic(args.workload, dom, args.scale)
     roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": kern[dom]["frac_of_measured_hbm"], "traffic": traffic,
                 "kernel": dom, "peak_source": peak_src,
@@ -465,7 +458,28 @@ def library_spmv(P, reps=20):
 
 
 KERNEL_FILES = {"xstep": ("common.cuh", "spmv.cuh"), "ystep": ("common.cuh", "spmv.cuh"),
-                "memory": ("common.cuh", "anderson.cuh"), "mix": ("common.cuh", "anderson.cuh")}
+                "memory": ("common.cuh", "anderson.cuh"), "mix": ("common.cuh", "anderson.cuh"),
+                "batch:xstep": ("common.cuh", "spmv.cuh", "batch.cuh"),
+                "batch:ystep": ("common.cuh", "spmv.cuh", "batch.cuh"),
+                "batch:memory": ("common.cuh", "anderson.cuh", "batch.cuh")}
+
+
+def committed_traffic(workload, kind, scale):
+    """DRAM bytes per launch of a kernel kind from the committed ncu figures
+    (profiles/traffic.json, full-size launch), or None when the workload is
+    scaled, no figure exists, or the kernel's sources changed since the
+    capture."""
+    if scale != 1.0:
+        return None
+    try:
+        tf = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+    except (OSError, ValueError):
+        return None
+    ent = tf.get(workload, {}).get(kind)
+    key = "batch:" + kind if workload == "batch" else kind
+    if not ent or key not in KERNEL_FILES or ent.get("kernel_sources") != kernel_source_hash(key):
+        return None
+    return ent["dram_bytes_per_launch"]
 
 
 def kernel_source_hash(kind):
@@ -608,7 +622,8 @@ def run_batch(args):
         kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
     dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: prof[k]["total_ms"])
     roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
-                "frac": kern[dom]["frac_of_measured_hbm"], "traffic": None, "kernel": dom,
+                "frac": kern[dom]["frac_of_measured_hbm"], "kernel": dom,
+                "traffic": committed_traffic("batch", dom, args.scale),
                 "peak_source": peak_src, "alg_bytes_per_launch": kern[dom]["alg_bytes_per_launch"]}
     b.close()
 

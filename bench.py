@@ -44,6 +44,11 @@ WORKLOADS = {
                        "2.1), N(0,1)*lognormal(0,3) per row, 20% '>=' rows, bounds [0,U(1,100)] "
                        "with 10% free; AA-PDHG m=20, FP32 SpMV/iterates + FP64-accurate "
                        "Gram/solve/safeguard/KKT"),
+    "banded": dict(method="aa", mem=20, precision="mixed",
+                   desc="diagnostic: the large sizes (2M x 5M, 50M nnz) with banded structure (row i "
+                        "holds 25 consecutive columns), values/senses/bounds as large; the "
+                        "half-steps' streaming ceiling when gathers share cache lines; AA-PDHG m=20, "
+                        "mixed precision"),
     "medium": dict(method="aa", mem=10, precision="mixed",
                    desc="100k x 300k CSR, ~2M nnz, log-normal row lengths (median 7, max 2000), "
                         "N(0,1)*lognormal(0,2) per row, 70/30 '='/'>=' rows, bounds [0,U(1,100)] "
@@ -90,10 +95,12 @@ def whole_job_rate(world, units_per_rank, t_max_ms):
 
 def make_problem(workload, rank, scale=1.0):
     import lpgen
-    seed = lpgen.SEED_BASE + {"tiny": 1, "medium": 2, "large": 3}[workload] + 1000 * rank
+    seed = lpgen.SEED_BASE + {"tiny": 1, "medium": 2, "large": 3, "banded": 5}[workload] + 1000 * rank
     if scale != 1.0 and workload == "large":
         return lpgen.large(seed=seed, m=int(2_000_000 * scale), n=int(5_000_000 * scale),
                            z=int(50_000_000 * scale))
+    if scale != 1.0 and workload == "banded":
+        return lpgen.banded(seed=seed, m=int(2_000_000 * scale), n=int(5_000_000 * scale))
     if scale != 1.0 and workload == "medium":
         return lpgen.medium(seed=seed, m=int(100_000 * scale), n=int(300_000 * scale))
     return lpgen.WORKLOADS[workload](seed=seed)

@@ -20,6 +20,11 @@ Workloads (sizes and distributions of the benchmark configurations):
   large   2M x 5M, Chung-Lu power-law row and column degrees (exponent 2.1)
           scaled to Z about 50M with duplicates removed, values N(0,1) times one
           lognormal(0,3) scale per row, 20% '>=' rows, bounds as medium.
+  banded  the large sizes (2M x 5M, Z = 50M) with local structure: row i holds
+          the 25 consecutive columns from floor(i (n - 25) / (m - 1)); values,
+          senses and bounds as large.  A diagnostic of the half-steps' streaming
+          ceiling (the gathered entries of a row share cache lines), not a
+          workload of the paper's kind.
 """
 from __future__ import annotations
 
@@ -238,6 +243,23 @@ def large(seed=SEED_BASE + 3, m=2_000_000, n=5_000_000, z=50_000_000, exponent=2
     return construct(rng, m, n, rp, ci, v, sense, l, u, name=f"large-{m}x{n}")
 
 
+def banded(seed=SEED_BASE + 5, m=2_000_000, n=5_000_000, row_len=25) -> Problem:
+    """m x n with row i holding the row_len consecutive columns starting at
+    floor(i (n - row_len) / (m - 1)): every row has row_len entries and every
+    column about row_len m / n (fewer at the two ends), so the degrees are
+    nearly uniform and a longest-first renumbering keeps the columns of a
+    degree class in order.  Values N(0,1) times a lognormal(0,3) scale per
+    row, 20% '>=' rows, bounds as medium."""
+    rng = np.random.default_rng(seed)
+    start = (np.arange(m, dtype=np.int64) * (n - row_len)) // max(m - 1, 1)
+    ci = (start[:, None] + np.arange(row_len, dtype=np.int64)[None, :]).astype(np.int32).ravel()
+    rp = np.arange(m + 1, dtype=np.int64) * row_len
+    v = rng.standard_normal(m * row_len) * np.repeat(np.exp(rng.normal(0.0, 3.0, m)), row_len)
+    sense = (rng.random(m) < 0.20).astype(np.int8)
+    l, u = _bounds_medium(rng, n)
+    return construct(rng, m, n, rp, ci, v, sense, l, u, name=f"banded-{m}x{n}")
+
+
 def batch_member(seed, m, n_per_m=2.5, nnz_mean=8.0, len_sigma=0.8) -> Problem:
     """One LP of the batched workload: m rows, round(n_per_m * m) columns, row
     lengths lognormal with mean nnz_mean (clipped to [1, min(2000, n)]) at
@@ -293,4 +315,4 @@ def from_dense(Kd, sense, q, c, l, u, name="dense") -> Problem:
                    np.asarray(l, np.float64), np.asarray(u, np.float64), name=name)
 
 
-WORKLOADS = {"tiny": tiny, "medium": medium, "large": large}
+WORKLOADS = {"tiny": tiny, "medium": medium, "large": large, "banded": banded}

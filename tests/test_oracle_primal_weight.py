@@ -83,8 +83,8 @@ def test_memory_reset_restarts_anderson():
 def test_dhat_blend_picks_alpha_by_residual_decrease(rho_min):
     # omega stays 1 (theta = 0, tau = sigma), so the blend is
     # (1 - alpha) I + alpha D-hat_base: with alpha_dec = 0 and alpha_inc = 1 the
-    # run after u^K must equal a fresh run with D-hat = I (decrease judged
-    # sufficient) or with the base D-hat (judged insufficient)
+    # run after u^K must equal a fresh run with D-hat = I (decrease deemed
+    # sufficient) or with the base D-hat (deemed insufficient)
     P, lp = _lp()
     kw = dict(method=1, mem=5, tau=0.05, sigma=0.05, D=1e30)
     run1 = O.solve(lp, O.Params(**kw, pw_period=K, pw_theta=0.0, pw_dhat=1, pw_rho_min=rho_min,

@@ -594,9 +594,11 @@ template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
     if (kkt) launch_x<V, true>(h, h->shape_x, mode);
     else launch_x<V, false>(h, h->shape_x, mode);
     mark_end(h);
-    mark_begin(h, KIND_YSTEP);
+    mark_begin(h, KIND_YSTEP);                 // the y-step and its final reduction
     if (kkt) launch_y<V, true>(h, h->shape_y, mode);
     else launch_y<V, false>(h, h->shape_y, mode);
+    k_finalize<V><<<1, BLOCK, 0, h->stream>>>(prob<V>(h), h->mp, mode, kkt ? 1 : 0);
+    h->launches += 1;
     mark_end(h);
 }
 
@@ -695,7 +697,7 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
     for (auto &g : h->graphs)
         if (g.phase == phase && g.kkt_every == kkt_every && g.tol == tol) {
             if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
-            h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 4 : 3);
+            h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 5 : 4);
             return true;
         }
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -728,7 +730,7 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
     }
     h->graphs.push_back({exec, phase, kkt_every, tol});
     if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
-    h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 4 : 3);
+    h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 5 : 4);
     return true;
 }
 

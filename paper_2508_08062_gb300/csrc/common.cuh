@@ -119,7 +119,6 @@ struct DevState {
     int32_t restart;       // primal weight update: this iteration restarts the memory
     double kkt[6];         // r_p, r_d, r_g, KKT, c'x, dual objective at u^k
     int32_t kkt_valid;
-    uint32_t cnt_spmv;     // last-block counter of the y-step
     uint32_t cnt_ring;     // last-block counter of the memory pass
     uint32_t cnt_norm;     // last-block counter of the norm kernels
     double scratch[8];

@@ -294,7 +294,8 @@ template <typename V, bool KKT> struct EpiY {
 };
 
 // Final reduction after both half-steps (one block): ||g^k||, KKT of u^k,
-// termination flag, safeguard decision of Alg. 2 / Alg. 3.
+// termination flag, safeguard decision of Alg. 2 / Alg. 3.  Reads the block
+// partials of the x-step (part1, grid1 blocks) and the y-step (part2).
 template <typename V>
 __device__ void finalize_T(const Prob<V> &P, const MethodParams &mp, int mode, bool kkt) {
     __shared__ double sh[WARPS * 4];
@@ -372,7 +373,15 @@ __global__ void __launch_bounds__(BLOCK) k_ystep(Prob<V> P, MethodParams mp, int
         Acc<V> a1[1] = {g2};
         block_reduce_store<V, 1>(a1, sh, P.part2 + (int64_t)blockIdx.x * 3);
     }
-    if (last_block(&P.st->cnt_spmv)) finalize_T<V>(P, mp, mode, KKT);
+}
+
+// The final reduction after both half-steps, one block of its own: a
+// last-block test in the y-step would have its ~900 co-resident blocks, which
+// finish together, contend on one counter at the kernel's end.
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_finalize(Prob<V> P, MethodParams mp, int mode, int kkt) {
+    if (mode < MODE_EVAL && (P.st->done | P.st->error)) return;   // as the half-steps
+    finalize_T<V>(P, mp, mode, kkt != 0);
 }
 
 // --------------------------------------------------------------------------

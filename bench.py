@@ -551,6 +551,8 @@ def run_batch(args):
         nrm = b.estimate_norms(100, seed=1)
         b.set_steps(0.9 / nrm, 0.9 / nrm)
         b.set_method("aa", mem=M, D=10.0, eps=1.0)
+        if args.primal_weight:
+            b.set_primal_weight(period=args.primal_weight)
 
     b = BatchSolver(members, precision="mixed", stream=stream)
     prepare(b)
@@ -663,6 +665,8 @@ def run_batch(args):
                 nrm = s.estimate_norm(100, seed=1)
                 s.set_steps(0.9 / nrm, 0.9 / nrm)
                 s.set_method("aa", mem=M, D=10.0, eps=1.0)
+                if args.primal_weight:
+                    s.set_primal_weight(period=args.primal_weight)
                 barrier()
                 t0 = time.perf_counter()
                 c, n = s.iterate(args.batch_max_iters, tol=tol, kkt_every=kkt_every)
@@ -676,13 +680,13 @@ def run_batch(args):
                   "sample_rows": [int(members[p].m) for p in pick],
                   "sample_seconds": [round(t, 4) for t in times], "sample_iterations": iters,
                   "sample_converged": ok, "estimated_seconds_all": est,
-                  "note": "FP64 single-LP solver (same scaling, step rule, AA m=10, KKT every 64, "
-                          "same iteration cap), solve time per LP, stratified by size; time for "
-                          "all = mean x 256; solves/s counts converged LPs only"}
+                  "note": "FP64 single-LP solver (same scaling, step rule, AA m=10, primal weight "
+                          "setting, KKT every 64, same iteration cap), solve time per LP, stratified "
+                          "by size; time for all = mean x 256; solves/s counts converged LPs only"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_batch(members, st, M)
+        cpu = cpu_baseline_batch(members, st, M, pw_period=args.primal_weight)
 
     if rank == 0:
         fin = done_at[~np.isnan(done_at)]
@@ -693,6 +697,7 @@ def run_batch(args):
             "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded generator, known optimum per LP; one batch per rank)",
             "config": {"workload": "batch", "desc": wl["desc"], "nprob": nprob,
+                       "primal_weight_period": args.primal_weight,
                        "rows": int(sum(P.m for P in members)), "cols": int(sum(P.n for P in members)),
                        "nnz": int(Ztot), "scale": args.scale, "memory": M, "kkt_every": kkt_every,
                        "tol": tol, "parallelism": f"replicas{world}",
@@ -750,6 +755,8 @@ def run_serve(args):
     ids = []
     with Server(method="aa", mem=M, max_cohorts=args.max_cohorts,
                 max_cohort_size=args.cohort_size, max_iters=args.serve_max_iters) as srv:
+        if args.primal_weight:
+            srv.set_primal_weight(period=args.primal_weight)
         with ClockSampler(dev_id) as clk:
             t0 = time.perf_counter()
             k = 0
@@ -791,6 +798,8 @@ def run_serve(args):
                     nrm = s1.estimate_norm(100, seed=1)
                     s1.set_steps(0.9 / nrm, 0.9 / nrm)
                     s1.set_method("aa", mem=M, D=10.0, eps=1.0)
+                    if args.primal_weight:
+                        s1.set_primal_weight(period=args.primal_weight)
                     torch.cuda.synchronize()
                     ts = time.perf_counter()
                     c, n_it = s1.iterate(args.serve_max_iters, tol=tv, kkt_every=64)
@@ -826,7 +835,8 @@ def run_serve(args):
         "data": "synthetic (seeded generator, known optimum per LP)",
         "config": {"workload": "serve", "desc": wl["desc"], **stream_desc,
                    "max_cohorts": args.max_cohorts, "cohort_size": args.cohort_size,
-                   "max_iters_per_lp": args.serve_max_iters, "scale": args.scale},
+                   "max_iters_per_lp": args.serve_max_iters, "scale": args.scale,
+                   "primal_weight_period": args.primal_weight},
         "completed": {s_: states.count(s_) for s_ in set(states)},
         "converged_by_tol": per_tol, "wall_s": wall,
         "p50_latency_s": float(np.percentile(lat, 50)) if len(lat) else None,
@@ -841,7 +851,7 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
-def cpu_baseline_batch(members, st, M, budget_s=20.0):
+def cpu_baseline_batch(members, st, M, budget_s=20.0, pw_period=0):
     """The FP64 oracle as it stands on one median-size member of the batch
     (scaled as the GPU run scales it), timed for a bounded number of AA-PDHG
     iterations; solves/s of the batch are then estimated from the oracle's
@@ -857,7 +867,7 @@ def cpu_baseline_batch(members, st, M, budget_s=20.0):
     S = O.scaled_lp(lp, *O.scaling(lp, 10, True))
     K = sp.csr_matrix((S.v, S.ci.astype(np.int64), S.rp), shape=(P.m, P.n))
     tau = 0.9 / svds(K, k=1, return_singular_vectors=False, random_state=0, maxiter=200, tol=1e-3)[0]
-    prm = O.Params(method=1, mem=M, tau=tau, sigma=tau, D=10.0, eps=1.0)
+    prm = O.Params(method=1, mem=M, tau=tau, sigma=tau, D=10.0, eps=1.0, pw_period=pw_period)
     t0 = time.perf_counter()
     O.solve(S, prm, 10)
     t1 = (time.perf_counter() - t0) / 10

@@ -339,6 +339,18 @@ aapdhg_status aapdhg_batch_set_method(aapdhg_batch_t h, int32_t method, int32_t 
 /* As aapdhg_set_scaling, each problem scaled on its own rows and columns.    */
 aapdhg_status aapdhg_batch_set_scaling(aapdhg_batch_t h, int32_t ruiz_iters, int32_t pock_chambolle);
 
+/* As aapdhg_set_primal_weight, for every problem of the batch on its own:
+ * each problem's gamma and omega^0 come from its own steps, and at every
+ * batch iterate u^k with k = 0 mod U_P each running problem measures its own
+ * Delta_x, Delta_y, and updates its own omega, steps, D-hat and memory (or
+ * leaves them when a Delta is <= eps_zero).  The update runs on the device
+ * (no host round trip; aapdhg_batch_launch stays asynchronous).  A problem
+ * that stops at the update iterate keeps that iterate.  Same parameter
+ * ranges and errors as aapdhg_set_primal_weight.  Resets the run.          */
+aapdhg_status aapdhg_batch_set_primal_weight(aapdhg_batch_t h, int64_t period, double theta,
+                                             double eps_zero, int32_t dhat_blend, double rho_min,
+                                             double alpha_dec, double alpha_inc);
+
 /* Starts of all problems (concatenated caller-order x0: sum(n[p]), y0:
  * sum(m[p]); NULL = zeros), projected as in aapdhg_set_start; resets.        */
 aapdhg_status aapdhg_batch_set_start(aapdhg_batch_t h, const double *x0, const double *y0);
@@ -445,6 +457,12 @@ aapdhg_status aapdhg_server_submit(aapdhg_server_t s, int32_t m, int32_t n, int6
                                    const double *val, const int8_t *row_sense, const double *q,
                                    const double *c, const double *lb, const double *ub, double tol,
                                    int64_t *id);
+/* Primal weight update (as aapdhg_batch_set_primal_weight) for the cohorts
+ * admitted after the call; period 0 switches it off for them.  Parameters out
+ * of range: AAPDHG_ERR_INVALID, not sticky.                                 */
+aapdhg_status aapdhg_server_set_primal_weight(aapdhg_server_t s, int64_t period, double theta,
+                                              double eps_zero, int32_t dhat_blend, double rho_min,
+                                              double alpha_dec, double alpha_inc);
 aapdhg_status aapdhg_server_step(aapdhg_server_t s, int32_t *running, int32_t *waiting);
 aapdhg_status aapdhg_server_result(aapdhg_server_t s, int64_t id, int32_t *state, double *x,
                                    double *y, double *kkt6, int64_t *iters, double *times3);

@@ -38,10 +38,12 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_set_primal_weight",
            "aapdhg_batch_set_task_shape", "aapdhg_batch_set_tolerances", "aapdhg_batch_launch",
            "aapdhg_batch_poll", "aapdhg_server_create", "aapdhg_server_submit",
-           "aapdhg_server_step", "aapdhg_server_result", "aapdhg_server_device_bytes",
+           "aapdhg_server_step", "aapdhg_server_set_primal_weight", "aapdhg_server_result",
+           "aapdhg_server_device_bytes",
            "aapdhg_server_last_error", "aapdhg_server_destroy",
            "aapdhg_batch_create", "aapdhg_batch_set_steps", "aapdhg_batch_estimate_norms",
-           "aapdhg_batch_set_method", "aapdhg_batch_set_scaling", "aapdhg_batch_set_start",
+           "aapdhg_batch_set_method", "aapdhg_batch_set_scaling", "aapdhg_batch_set_primal_weight",
+           "aapdhg_batch_set_start",
            "aapdhg_batch_reset", "aapdhg_batch_iterate", "aapdhg_batch_get_iterate",
            "aapdhg_batch_get_kkt", "aapdhg_batch_get_status", "aapdhg_batch_profile_kernels",
            "aapdhg_batch_get_kernel_profile", "aapdhg_batch_device_bytes",
@@ -106,6 +108,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_server_create.argtypes = [i32, i32, i32, i32, i64, i64, C.POINTER(vp)]
     L.aapdhg_server_submit.argtypes = [vp, i32, i32, i64] + [vp] * 8 + [f64, C.POINTER(i64)]
     L.aapdhg_server_step.argtypes = [vp, vp, vp]
+    L.aapdhg_server_set_primal_weight.argtypes = [vp, i64, f64, f64, i32, f64, f64, f64]
     L.aapdhg_server_result.argtypes = [vp, i64, vp, vp, vp, vp, vp, vp]
     L.aapdhg_server_device_bytes.argtypes = [vp, C.POINTER(i64)]
     L.aapdhg_server_last_error.argtypes = [vp]
@@ -117,6 +120,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_batch_set_method.argtypes = [vp, i32, i32, f64, f64, f64, f64, f64, f64, f64, i32,
                                           i32]
     L.aapdhg_batch_set_scaling.argtypes = [vp, i32, i32]
+    L.aapdhg_batch_set_primal_weight.argtypes = [vp, i64, f64, f64, i32, f64, f64, f64]
     L.aapdhg_batch_set_start.argtypes = [vp, vp, vp]
     L.aapdhg_batch_reset.argtypes = [vp]
     L.aapdhg_batch_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
@@ -444,6 +448,15 @@ class BatchSolver:
         self._check(self._L.aapdhg_batch_set_scaling(self._h, int(ruiz_iters),
                                                      int(bool(pock_chambolle))))
 
+    def set_primal_weight(self, period=3000, theta=0.5, eps_zero=1e-10, dhat_blend=True,
+                          rho_min=0.1, alpha_dec=0.1, alpha_inc=0.9):
+        """Periodic primal weight update of every problem on its own (period 0:
+        off); resets the run."""
+        self._check(self._L.aapdhg_batch_set_primal_weight(self._h, int(period), float(theta),
+                                                           float(eps_zero), int(bool(dhat_blend)),
+                                                           float(rho_min), float(alpha_dec),
+                                                           float(alpha_inc)))
+
     def set_start(self, x0=None, y0=None):
         """x0, y0: concatenated caller-order arrays, or lists of per-problem arrays."""
         if isinstance(x0, (list, tuple)):
@@ -552,6 +565,14 @@ class Server:
     def _check(self, s):
         if s != OK:
             raise AAPDHGError(s, self._L.aapdhg_server_last_error(self._h).decode())
+
+    def set_primal_weight(self, period=3000, theta=0.5, eps_zero=1e-10, dhat_blend=True,
+                          rho_min=0.1, alpha_dec=0.1, alpha_inc=0.9):
+        """Primal weight update for the cohorts admitted from now on (0: off)."""
+        self._check(self._L.aapdhg_server_set_primal_weight(self._h, int(period), float(theta),
+                                                            float(eps_zero), int(bool(dhat_blend)),
+                                                            float(rho_min), float(alpha_dec),
+                                                            float(alpha_inc)))
 
     def close(self):
         if self._h:

@@ -87,6 +87,16 @@ struct aapdhg_batch_s {
     bool tuned = false, autotune = true;
     int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
     double tune_us[2 * NSHAPE] = {};
+    // primal weight update (off when pw_period = 0): per problem gamma, omega
+    // (pw_w), the blend weight and update flag of the last try, the snapshot
+    // of u at the last update point, the base D-hat
+    int64_t pw_period = 0, pw_last_g = -1;
+    PwParams pw{0.5, 1e-10, 0.1, 0.1, 0.9};
+    int32_t pw_dhat = 1;
+    void *pw_snap = nullptr, *pw_dh_base = nullptr;
+    double *pw_part = nullptr, *pw_w = nullptr, *pw_alpha = nullptr;
+    int32_t *pw_upd = nullptr;
+    bool pw_base_valid = false;            // pw_dh_base holds the current base D-hat
     // instrumentation
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;
@@ -303,6 +313,31 @@ template <typename V> aapdhg_status bensure_rings(bh_t h) {
     return AAPDHG_OK;
 }
 
+// The given steps of every problem into the device arrays (FP64 and the
+// iterate precision).
+aapdhg_status bupload_steps(bh_t h) {
+    const double *dt = h->prec == AAPDHG_FP64 ? h->bd.tau : h->bf.tau;
+    const double *ds = h->prec == AAPDHG_FP64 ? h->bd.sigma : h->bf.sigma;
+    BCK(h, cudaMemcpyAsync(const_cast<double *>(dt), h->tau.data(), 8 * (size_t)h->nprob, cudaMemcpyHostToDevice,
+                           h->stream));
+    BCK(h, cudaMemcpyAsync(const_cast<double *>(ds), h->sigma.data(), 8 * (size_t)h->nprob,
+                           cudaMemcpyHostToDevice, h->stream));
+    if (h->prec == AAPDHG_FP64) {
+        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.tau_v), h->tau.data(), 8 * (size_t)h->nprob,
+                               cudaMemcpyHostToDevice, h->stream));
+        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.sigma_v), h->sigma.data(), 8 * (size_t)h->nprob,
+                               cudaMemcpyHostToDevice, h->stream));
+    } else {
+        h->tau_f.assign(h->tau.begin(), h->tau.end());
+        h->sigma_f.assign(h->sigma.begin(), h->sigma.end());
+        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.tau_v), h->tau_f.data(), 4 * (size_t)h->nprob,
+                               cudaMemcpyHostToDevice, h->stream));
+        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.sigma_v), h->sigma_f.data(), 4 * (size_t)h->nprob,
+                               cudaMemcpyHostToDevice, h->stream));
+    }
+    return AAPDHG_OK;
+}
+
 // Start of every problem: u^0 (projected start, scaled when the LP is) in
 // component 0, state cleared, batch counter at 0.
 template <typename V> aapdhg_status breset(bh_t h) {
@@ -326,6 +361,27 @@ template <typename V> aapdhg_status breset(bh_t h) {
     }
     BCK(h, cudaMemcpyAsync(P.UP, up.data(), sizeof(V2) * h->N, cudaMemcpyHostToDevice, h->stream));
     BCK(h, cudaMemsetAsync(h->stb, 0, sizeof(DevState) * h->nprob, h->stream));
+    if (h->pw_period > 0) {
+        // a run starts with the given steps, omega^0 = sqrt(sigma / tau),
+        // gamma = sqrt(tau sigma) and the base D-hat (R13)
+        aapdhg_status s = bupload_steps(h);
+        if (s != AAPDHG_OK) return s;
+        std::vector<double> w(2 * (size_t)h->nprob);
+        for (int32_t p = 0; p < h->nprob; ++p) {
+            const double t = h->tau[p], sg = h->sigma[p];
+            w[2 * p] = t > 0 ? sqrt(t * sg) : 0.0;
+            w[2 * p + 1] = t > 0 ? sqrt(sg / t) : 1.0;
+        }
+        BCK(h, cudaMemcpyAsync(h->pw_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, h->stream));
+        V *dh = const_cast<V *>(P.dh);
+        if (!h->pw_base_valid) {
+            BCK(h, cudaMemcpyAsync(h->pw_dh_base, dh, sizeof(V) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+            h->pw_base_valid = true;
+        } else {
+            BCK(h, cudaMemcpyAsync(dh, h->pw_dh_base, sizeof(V) * h->N, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        h->pw_last_g = -1;
+    }
     BCK(h, cudaStreamSynchronize(h->stream));
     h->g = 0;
     return AAPDHG_OK;
@@ -524,6 +580,11 @@ template <typename V> aapdhg_status bbegin(bh_t h, double tol, int32_t kkt_every
     if (h->mp.method != 0 && h->mp.mem > 0 && (s = bensure_rings<V>(h)) != AAPDHG_OK) return s;
     if (h->autotune && !h->tuned && (s = bautotune<V>(h)) != AAPDHG_OK) return s;
     if (h->g == 0) {
+        if (h->pw_period > 0) {                  // snapshot u^0 for the first update
+            k_pw_delta_b<V><<<bview<V>(h).nchunk, BLOCK, 0, h->stream>>>(
+                bprob<V>(h).UP, (V *)h->pw_snap, bview<V>(h), 0, 1, h->pw_part);
+            h->launches += 1;
+        }
         blaunch_iteration<V>(h, 0, MODE_ITER);   // u^1 = T u^0 and g^0 of every problem
         h->g = 1;
     } else {
@@ -534,12 +595,46 @@ template <typename V> aapdhg_status bbegin(bh_t h, double tol, int32_t kkt_every
     return AAPDHG_OK;
 }
 
-// Enqueue n batch iterations (a CUDA graph when n is a full chunk).
-template <typename V> aapdhg_status blaunch_chunk(bh_t h, int64_t n) {
-    if (!(n == B_CHUNK_ITERS && blaunch_chunk_graph<V>(h, h->g)))
-        for (int64_t c = 0; c < n; ++c) blaunch_iteration<V>(h, h->g + c, MODE_ITER);
+// Primal weight update of every running problem at its iterate u^k, k = h->g
+// (the iteration about to be launched works on u^g): enqueued only.
+template <typename V> aapdhg_status bpw_update(bh_t h) {
+    Prob<V> &P = bprob<V>(h);
+    BatchView<V> &B = bview<V>(h);
+    const int cur = (int)(h->g & 1);
+    k_pw_delta_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(P.UP, (V *)h->pw_snap, B, cur, 0, h->pw_part);
+    k_pw_apply_b<V><<<(h->nprob + 127) / 128, 128, 0, h->stream>>>(B, h->pw_part, h->pw_w, h->pw_alpha,
+                                                                    h->pw_upd, h->pw);
+    h->launches += 2;
+    if (h->pw_dhat) {
+        k_dhat_blend_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(const_cast<V *>(P.dh), (const V *)h->pw_dh_base, B,
+                                                              h->pw_w, h->pw_alpha, h->pw_upd);
+        h->launches += 1;
+    }
     BCK(h, cudaGetLastError());
-    h->g += n;
+    return AAPDHG_OK;
+}
+
+// Enqueue n batch iterations (CUDA graphs for full chunks); with the primal
+// weight update on, the run is cut at the update points k = 0 mod U_P, each
+// update enqueued before its iteration.
+template <typename V> aapdhg_status blaunch_chunk(bh_t h, int64_t n) {
+    while (n > 0) {
+        int64_t c = n;
+        if (h->pw_period > 0) {
+            const int64_t r = h->g % h->pw_period;
+            if (r == 0 && h->pw_last_g != h->g) {
+                aapdhg_status s = bpw_update<V>(h);
+                if (s != AAPDHG_OK) return s;
+                h->pw_last_g = h->g;
+            }
+            c = std::min<int64_t>(c, h->pw_period - r);
+        }
+        if (!(c == B_CHUNK_ITERS && blaunch_chunk_graph<V>(h, h->g)))
+            for (int64_t i = 0; i < c; ++i) blaunch_iteration<V>(h, h->g + i, MODE_ITER);
+        BCK(h, cudaGetLastError());
+        h->g += c;
+        n -= c;
+    }
     return AAPDHG_OK;
 }
 
@@ -711,6 +806,7 @@ template <typename V> aapdhg_status bset_scaling(bh_t h, int32_t ruiz_iters, int
     k_dhat<V><<<gr, BLOCK, 0, s>>>(P.KT, P.K, P.n, P.m, h->dhat_mode < 0 ? 1 : h->dhat_mode,
                                    const_cast<V *>(P.dh));
     BCK(h, cudaGetLastError());
+    h->pw_base_valid = false;
     h->scaled = true;
     return AAPDHG_OK;
 }
@@ -884,19 +980,8 @@ aapdhg_status aapdhg_batch_set_steps(aapdhg_batch_t h, const double *tau, const 
             return bfail(h, AAPDHG_ERR_INVALID, "tau and sigma must be finite and > 0");
     h->tau.assign(tau, tau + h->nprob);
     h->sigma.assign(sigma, sigma + h->nprob);
-    const double *dt = h->prec == AAPDHG_FP64 ? h->bd.tau : h->bf.tau;
-    const double *ds = h->prec == AAPDHG_FP64 ? h->bd.sigma : h->bf.sigma;
-    BCK(h, cudaMemcpyAsync(const_cast<double *>(dt), tau, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-    BCK(h, cudaMemcpyAsync(const_cast<double *>(ds), sigma, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-    if (h->prec == AAPDHG_FP64) {
-        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.tau_v), tau, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-        BCK(h, cudaMemcpyAsync(const_cast<double *>(h->bd.sigma_v), sigma, 8 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-    } else {
-        h->tau_f.assign(tau, tau + h->nprob);
-        h->sigma_f.assign(sigma, sigma + h->nprob);
-        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.tau_v), h->tau_f.data(), 4 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-        BCK(h, cudaMemcpyAsync(const_cast<float *>(h->bf.sigma_v), h->sigma_f.data(), 4 * (size_t)h->nprob, cudaMemcpyHostToDevice, h->stream));
-    }
+    aapdhg_status s = bupload_steps(h);
+    if (s != AAPDHG_OK) return s;
     bdrop_graphs(h);
     return breset_any(h);
 }
@@ -932,6 +1017,7 @@ aapdhg_status aapdhg_batch_set_method(aapdhg_batch_t h, int32_t method, int32_t 
                                                        const_cast<float *>(h->pf.dh));
         BCK(h, cudaGetLastError());
         h->dhat_mode = dhat_mode;
+        h->pw_base_valid = false;
     }
     return breset_any(h);
 }
@@ -945,6 +1031,44 @@ aapdhg_status aapdhg_batch_set_scaling(aapdhg_batch_t h, int32_t ruiz_iters, int
     aapdhg_status s = h->prec == AAPDHG_FP64 ? bset_scaling<double>(h, ruiz_iters, pock_chambolle)
                                              : bset_scaling<float>(h, ruiz_iters, pock_chambolle);
     if (s != AAPDHG_OK) return s;
+    return breset_any(h);
+}
+
+aapdhg_status aapdhg_batch_set_primal_weight(aapdhg_batch_t h, int64_t period, double theta, double eps_zero,
+                                             int32_t dhat_blend, double rho_min, double alpha_dec,
+                                             double alpha_inc) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (period < 0 || !(theta >= 0 && theta <= 1) || !(eps_zero >= 0) || !std::isfinite(rho_min) ||
+        !(alpha_dec >= 0 && alpha_dec <= 1) || !(alpha_inc >= 0 && alpha_inc <= 1))
+        return bfail(h, AAPDHG_ERR_INVALID, "primal weight parameters out of range");
+    const size_t sv = h->prec == AAPDHG_FP64 ? 8 : 4;
+    if (period > 0) {
+        const int32_t nchunk = h->prec == AAPDHG_FP64 ? h->bd.nchunk : h->bf.nchunk;
+        if (!h->pw_snap) h->pw_snap = bdev_alloc(h, sv * h->N);
+        if (!h->pw_dh_base) {
+            h->pw_dh_base = bdev_alloc(h, sv * h->N);
+            h->pw_base_valid = false;
+        }
+        if (!h->pw_part) h->pw_part = (double *)bdev_alloc(h, sizeof(double) * std::max(nchunk, 1));
+        if (!h->pw_w) h->pw_w = (double *)bdev_alloc(h, sizeof(double) * 2 * h->nprob);
+        if (!h->pw_alpha) h->pw_alpha = (double *)bdev_alloc(h, sizeof(double) * h->nprob);
+        if (!h->pw_upd) h->pw_upd = (int32_t *)bdev_alloc(h, sizeof(int32_t) * h->nprob);
+        if (!h->pw_snap || !h->pw_dh_base || !h->pw_part || !h->pw_w || !h->pw_alpha || !h->pw_upd)
+            return bfail(h, AAPDHG_ERR_OOM, "primal weight buffers");
+    } else if (h->pw_period > 0) {
+        // back to fixed steps: the given steps and the base D-hat
+        aapdhg_status s = bupload_steps(h);
+        if (s != AAPDHG_OK) return s;
+        if (h->pw_base_valid)
+            BCK(h, cudaMemcpyAsync(h->prec == AAPDHG_FP64 ? (void *)h->pd.dh : (void *)h->pf.dh, h->pw_dh_base,
+                                   sv * (size_t)h->N, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    h->pw_period = period;
+    h->pw = PwParams{theta, eps_zero, rho_min, alpha_dec, alpha_inc};
+    h->pw_dhat = dhat_blend ? 1 : 0;
+    h->bf.pw_on = h->bd.pw_on = period > 0 ? 1 : 0;
+    bdrop_graphs(h);
     return breset_any(h);
 }
 

@@ -53,6 +53,7 @@ template <typename V> struct BatchView {
     uint32_t *pcnt;                   // per-problem arrival counters (self-resetting)
     const double *pnorm;              // per problem: ||q||, ||c|| of the caller's LP
     const double *ptol;               // per-problem tolerances, or null (one tolerance for all)
+    int32_t pw_on;                    // primal weight update on: ||g^k|| also without a memory
 };
 
 __device__ __forceinline__ bool stopped(const DevState *s) { return (s->done | s->error) != 0; }
@@ -270,22 +271,26 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
         return;
     }
     const bool init = !st->init_done;
+    // the iteration of a primal weight update restarts the problem's memory:
+    // a plain step, g^k kept as the previous residual, no column across it
+    const bool restart = !init && st->restart;
     const int M = (mp.method == 0) ? 0 : mp.mem;
-    if (M == 0) return;
+    if (M == 0 && !B.pw_on) return;
+    const bool fresh = init || restart || M == 0;   // only g^k and ||g^k||^2
     __shared__ int64_t s_off[NSLOT];
     __shared__ int s_nold, s_new, s_prev_acc;
     __shared__ double sh[WARPS * (MC + 4)];
     if (threadIdx.x == 0) {
-        const int cnt = init ? 0 : st->count;
+        const int cnt = fresh ? 0 : st->count;
         const int drop = (cnt == M) ? 1 : 0;
         s_nold = cnt - drop;
-        s_new = init ? 0 : st->free_slot;
-        s_prev_acc = init ? 0 : st->accept;
+        s_new = fresh ? 0 : st->free_slot;
+        s_prev_acc = fresh ? 0 : st->accept;
     }
     __syncthreads();
     if (threadIdx.x < NSLOT) {
         const int t = threadIdx.x;
-        const int drop = (!init && st->count == M) ? 1 : 0;
+        const int drop = (!fresh && st->count == M) ? 1 : 0;
         s_off[t] = (int64_t)(t < s_nold ? st->list[t + drop] : 0) * P.Npad;
     }
     __syncthreads();
@@ -295,8 +300,9 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2; MC+3: ||g||^2
     Acc<V> acc[MC + 4];
     const int64_t stride = (int64_t)BLOCK * W;
-    if (init) {
-        // g^0 = u^1 - u^0 (u^1 = T u^0 was just written into the other component)
+    if (fresh) {
+        // g^k = T u^k - u^k (at the start: g^0 = u^1 - u^0, u^1 = T u^0 just
+        // written into the other component)
         const V *UPs = reinterpret_cast<const V *>(P.UP);
         for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride) {
             const Pack<V, W> pa = ld<V, W>(UPs + 2 * e), pb = ld<V, W>(UPs + 2 * e + W);
@@ -351,16 +357,21 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     const int lane = threadIdx.x;
     if (st->error || st->done == 2) return;
     if (st->done) {                       // stopped at this iteration's KKT test: now frozen
-        if (lane == 0) st->done = 2;
+        if (lane == 0) {
+            st->done = 2;
+            st->restart = 0;              // an update at the stop iteration is not applied
+        }
         return;
     }
     const bool init = !st->init_done;
+    const bool restart = !init && st->restart;       // primal weight update (R15)
     const int M = (mp.method == 0) ? 0 : mp.mem;
+    const bool norm = M > 0 || (fp64 ? Bd.pw_on : Bf.pw_on);
     __shared__ int s_old[NSLOT];
     __shared__ double red[MC + 3];
     __shared__ double gsq;
     __shared__ SolveSmem sm;
-    const int cnt = init ? 0 : st->count;
+    const int cnt = (init || restart) ? 0 : st->count;
     const int drop = (M > 0 && cnt == M) ? 1 : 0;
     const int nold = cnt - drop;
     const int sn = init ? 0 : st->free_slot;
@@ -368,7 +379,7 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     // fixed-order sums over the problem's chunks: Gram row, ||dg||^2, <dg,g>,
     // ||du||^2, ||g||^2
     const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
-    if (M > 0) {
+    if (norm) {
         // lane k sums column k over the problem's chunks in chunk order: one
         // FP64 add per chunk and lane, no cross-lane tree (FP64 issue is the
         // scarce resource here)
@@ -382,12 +393,13 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
         }
     }
     __syncwarp();
-    const double gn = M > 0 ? sqrt(gsq) : 0.0;
+    const double gn = norm ? sqrt(gsq) : 0.0;
     if (init) {
         if (lane == 0) {
             if (!isfinite(gn)) st->error = 1;
             st->g0 = gn;
             st->gnorm = gn;
+            st->gnorm_prev = NAN;
             st->count = 0;
             st->new_slot = 0;
             st->free_slot = 0;
@@ -402,10 +414,26 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
         if (lane == 0) st->error = 1;
         return;
     }
+    if (restart) {                        // a plain step; the memory restarts from it
+        if (lane == 0) {
+            st->gnorm_prev = st->gnorm;
+            st->gnorm = gn;
+            st->count = 0;
+            st->new_slot = 0;
+            st->free_slot = 0;
+            st->accept = 0;
+            st->use_count = 0;
+            st->n_pd += 1;
+            st->restart = 0;
+            st->it += 1;
+        }
+        return;
+    }
     if (lane == 0) {                      // the safeguard on one lane
         bool want = false;
         if (mp.method != 0 && M > 0)
             want = gn <= mp.D * st->g0 * safeguard_factor(st, mp.c_div, mp.eps);
+        st->gnorm_prev = st->gnorm;
         st->gnorm = gn;
         st->want_aa = want ? 1 : 0;
     }
@@ -437,6 +465,85 @@ __global__ void __launch_bounds__(BLOCK) k_mix_b(Prob<V> P, BatchView<V> B, Meth
     const V beta = (V)mp.beta;
     for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += (int64_t)BLOCK * W)
         mix_elems<V, MC, W>(P, e, cur, beta, s_gam, s_off, k, Wf);
+}
+
+// --------------------------------------------------------------------------
+// Primal weight update of every running problem at an iterate u^k with
+// k = 0 mod U_P (Alg. "Primal weight update" and the Remark on its form;
+// readings R13-R15), on the device so that an asynchronous launch needs no
+// host round trip:
+//   k_pw_delta_b   per chunk: sum of (u^k - snapshot)^2 (the chunk is all x
+//                  or all y), the snapshot becomes u^k (copy_only: the start);
+//   k_pw_apply_b   per problem (one thread): Delta_x, Delta_y from its chunk
+//                  sums in chunk order; when both exceed epsilon_zero the new
+//                  omega, tau = gamma / omega, sigma = gamma omega, the blend
+//                  weight alpha from rho_k of ||g^{k-1}||, ||g^{k-2}|| (R14)
+//                  and the restart flag (R15);
+//   k_dhat_blend_b per chunk of an updated problem: D-hat =
+//                  (1 - alpha) diag(1/omega, omega) + alpha diag(D1/omega, D2 omega).
+// --------------------------------------------------------------------------
+struct PwParams {
+    double theta, eps_zero, rho_min, alpha_dec, alpha_inc;
+};
+
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_pw_delta_b(const typename Vec2<V>::T *UP, V *snap, BatchView<V> B,
+                                                      int cur, int copy_only, double *part) {
+    const int4 ch = B.chunk[blockIdx.x];
+    const bool run = copy_only || !stopped(B.stb + ch.x);
+    Acc<V> a[1];
+    if (run)
+        for (int64_t e = ch.y + (int64_t)threadIdx.x; e < (int64_t)ch.y + ch.z; e += BLOCK) {
+            const V u = comp<V>(UP[e], cur);
+            if (!copy_only) a[0].add_sq(u - snap[e]);
+            snap[e] = u;
+        }
+    if (copy_only) return;
+    __shared__ double sh[WARPS];
+    block_reduce_store<V, 1>(a, sh, part + blockIdx.x);
+}
+
+template <typename V>
+__global__ void k_pw_apply_b(BatchView<V> B, const double *part, double *pw, double *alpha, int32_t *upd,
+                             PwParams pp) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= B.nprob) return;
+    DevState *st = B.stb + p;
+    upd[p] = 0;
+    if (stopped(st)) return;
+    double dx = 0.0, dy = 0.0;
+    for (int c = B.pchunk0[p]; c < B.pchunk0[p + 1]; ++c) {
+        if (B.chunk[c].w == 0) dx += part[c];
+        else dy += part[c];
+    }
+    dx = sqrt(dx);
+    dy = sqrt(dy);
+    if (!(dx > pp.eps_zero && dy > pp.eps_zero)) return;   // omega unchanged, no restart
+    const double gamma = pw[2 * p];
+    const double omega = exp(pp.theta * log(dy / dx) + (1.0 - pp.theta) * log(pw[2 * p + 1]));
+    pw[2 * p + 1] = omega;
+    const double tau = gamma / omega, sigma = gamma * omega;
+    const_cast<double *>(B.tau)[p] = tau;
+    const_cast<double *>(B.sigma)[p] = sigma;
+    const_cast<V *>(B.tau_v)[p] = (V)tau;
+    const_cast<V *>(B.sigma_v)[p] = (V)sigma;
+    const double r1 = st->gnorm, r2 = st->gnorm_prev;
+    const double rho = isnan(r2) ? 0.0 : (r2 - r1) / fmax(r2, pp.eps_zero);
+    alpha[p] = rho >= pp.rho_min ? pp.alpha_dec : pp.alpha_inc;
+    st->restart = 1;
+    upd[p] = 1;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_dhat_blend_b(V *dh, const V *base, BatchView<V> B, const double *pw,
+                                                        const double *alpha, const int32_t *upd) {
+    const int4 ch = B.chunk[blockIdx.x];
+    if (!upd[ch.x]) return;
+    const double omega = pw[2 * ch.x + 1], a = alpha[ch.x];
+    for (int64_t e = ch.y + (int64_t)threadIdx.x; e < (int64_t)ch.y + ch.z; e += BLOCK) {
+        const double b = (1.0 - a) + a * (double)base[e];
+        dh[e] = (V)(ch.w == 0 ? b / omega : b * omega);
+    }
 }
 
 // Per-problem status for the host: (iterations, AA steps, PDHG steps, done,

@@ -67,6 +67,10 @@ struct aapdhg_server_s {
     int64_t budget = 0;           // device bytes all cohorts may hold together
     int32_t kkt_every = 64;
     double mixed_tol_limit = 1e-5;  // tolerances below this are solved in FP64
+    // primal weight update of the cohorts admitted from now on (0: off)
+    int64_t pw_period = 0;
+    double pw_theta = 0.5, pw_eps = 1e-10, pw_rho_min = 0.1, pw_alpha_dec = 0.1, pw_alpha_inc = 0.9;
+    int32_t pw_dhat = 1;
     std::vector<Request> reqs;
     std::deque<int64_t> waiting[2];
     std::vector<Cohort> cohorts;
@@ -95,10 +99,11 @@ aapdhg_status sfail(aapdhg_server_t s, aapdhg_status st, const std::string &msg)
 // chunk / SELL copies (values and int32 indices), the iterate pairs and the
 // per-element vectors, the two Anderson rings (33 slots) and the scaling
 // buffers, in the cohort's precision.
-int64_t estimate_bytes(const Request &r) {
+int64_t estimate_bytes(const aapdhg_server_s *s, const Request &r) {
     const int64_t sv = r.prec == AAPDHG_FP64 ? 8 : 4;
     const int64_t Z = (int64_t)r.ci.size(), N = (int64_t)r.n + r.m + 8;
-    return 4 * Z * (4 + sv) + N * sv * (2 * 33 + 24) + 8 * (int64_t)(r.m + r.n) + 4096;
+    const int64_t pw = s->pw_period > 0 ? 2 * N * sv : 0;    // snapshot and base D-hat
+    return 4 * Z * (4 + sv) + N * sv * (2 * 33 + 24) + pw + 8 * (int64_t)(r.m + r.n) + 4096;
 }
 
 // Build one cohort from the first waiting requests of one precision class.
@@ -163,6 +168,9 @@ aapdhg_status admit(aapdhg_server_t s, int cls) {
     }
     if (st == AAPDHG_OK)
         st = aapdhg_batch_set_method(co.b, s->method, s->mem, 10.0, 1.0, 1e-10, 1.0, 0.2, 1e8, 1.0, 1, 1);
+    if (st == AAPDHG_OK && s->pw_period > 0)
+        st = aapdhg_batch_set_primal_weight(co.b, s->pw_period, s->pw_theta, s->pw_eps, s->pw_dhat,
+                                            s->pw_rho_min, s->pw_alpha_dec, s->pw_alpha_inc);
     if (st == AAPDHG_OK) st = aapdhg_batch_set_tolerances(co.b, tol.data());
     if (st == AAPDHG_OK) st = aapdhg_batch_device_bytes(co.b, &co.bytes);
     if (st != AAPDHG_OK) {
@@ -258,6 +266,26 @@ aapdhg_status aapdhg_server_create(int32_t method, int32_t m_A, int32_t max_coho
     return AAPDHG_OK;
 }
 
+aapdhg_status aapdhg_server_set_primal_weight(aapdhg_server_t s, int64_t period, double theta,
+                                              double eps_zero, int32_t dhat_blend, double rho_min,
+                                              double alpha_dec, double alpha_inc) {
+    if (!s) return AAPDHG_ERR_INVALID;
+    if (s->sticky) return s->sticky;
+    if (period < 0 || !(theta >= 0 && theta <= 1) || !(eps_zero >= 0) || !std::isfinite(rho_min) ||
+        !(alpha_dec >= 0 && alpha_dec <= 1) || !(alpha_inc >= 0 && alpha_inc <= 1)) {
+        s->err = "primal weight parameters out of range";
+        return AAPDHG_ERR_INVALID;                   // not sticky: the server goes on
+    }
+    s->pw_period = period;
+    s->pw_theta = theta;
+    s->pw_eps = eps_zero;
+    s->pw_dhat = dhat_blend ? 1 : 0;
+    s->pw_rho_min = rho_min;
+    s->pw_alpha_dec = alpha_dec;
+    s->pw_alpha_inc = alpha_inc;
+    return AAPDHG_OK;
+}
+
 aapdhg_status aapdhg_server_submit(aapdhg_server_t s, int32_t m, int32_t n, int64_t nnz,
                                    const int64_t *row_ptr, const int32_t *col_idx, const double *val,
                                    const int8_t *row_sense, const double *q, const double *c,
@@ -285,7 +313,7 @@ aapdhg_status aapdhg_server_submit(aapdhg_server_t s, int32_t m, int32_t n, int6
     r.ub.assign(ub, ub + n);
     r.tol = tol;
     r.prec = tol < s->mixed_tol_limit ? AAPDHG_FP64 : AAPDHG_MIXED;
-    r.est_bytes = estimate_bytes(r);
+    r.est_bytes = estimate_bytes(s, r);
     r.t_submit = now_s(s);
     *id = (int64_t)s->reqs.size();
     s->waiting[r.prec == AAPDHG_FP64 ? 1 : 0].push_back(*id);

@@ -340,3 +340,96 @@ def test_batch_task_shapes_give_identical_iterates():
             got.append(np.concatenate([np.concatenate(xy) for xy in b.get_iterate()]))
     for u in got[1:]:
         assert np.array_equal(u, got[0])
+
+
+# Primal weight update in the batch (Alg. "Primal weight update", readings
+# R13-R15): every problem updates on its own.  The members start from
+# different omega^0 (2 and 0.5); the LP without constraints never moves y, so
+# its update is always skipped (Delta_y = 0) and its trajectory is the plain one.
+PW_CASES = {
+    "aa5": dict(method=1, mem=5),
+    "faa6": dict(method=2, mem=6),
+    "pdhg": dict(method=0, mem=0),
+    "aa5_theta1_noblend": dict(method=1, mem=5, pw_theta=1.0, pw_dhat=0),
+}
+# Member 4 (5 x 9) amplifies 1e-15 perturbations of the steps to ~1.5e-9 over
+# these 160 iterations under AA / FAA with the update (oracle against itself),
+# so its iterates are not compared at 1e-9 there.
+PW_CHECKED = {"aa5": (0, 1, 2, 3, 5), "faa6": (0, 1, 2, 3, 5), "aa5_theta1_noblend": (0, 1, 2, 3, 5)}
+
+
+def _pw_steps(probs):
+    t = np.array([0.9 / _norm(P) for P in probs])
+    w0 = np.array([2.0 if p % 2 == 0 else 0.5 for p in range(len(probs))])
+    return t / w0, t * w0
+
+
+@pytest.mark.parametrize("name", list(PW_CASES))
+def test_fp64_batch_primal_weight_iterates_match_oracle(name):
+    iters, period = 160, 40
+    probs = _members() + [_box()]
+    checked = PW_CHECKED.get(name, range(len(probs)))
+    taus, sigs = _pw_steps(probs)
+    kw = PW_CASES[name]
+    refs = [O.solve(O.OracleLP.from_problem(P), O.Params(tau=t, sigma=s, pw_period=period, **kw), iters,
+                    rec_len=iters + 1, trace=True) for P, t, s in zip(probs, taus, sigs)]
+    prm = O.Params(tau=1.0, sigma=1.0, pw_period=period, **kw)
+    with _batch(probs) as b:
+        b.set_steps(taus, sigs)
+        _set_method(b, prm)
+        b.set_primal_weight(period=period, theta=prm.pw_theta, eps_zero=prm.pw_eps_zero,
+                            dhat_blend=bool(prm.pw_dhat), rho_min=prm.pw_rho_min)
+        b.iterate(0)
+        for k in range(iters + 1):
+            got = b.get_iterate()
+            for p, (x, y) in enumerate(got):
+                if p in checked:
+                    err = _rel(np.concatenate([x, y]), refs[p].rec_u[k])
+                    assert err <= FP64_TOL, (name, p, k, err)
+            if k < iters:
+                b.iterate(1)
+        st = b.status()
+    for p, r in enumerate(refs):
+        assert st[p, 0] == iters, (p, st[p])
+        if p in checked:
+            assert st[p, 1] == r.aa_steps and st[p, 2] == r.pdhg_steps, (name, p, st[p])
+        # the update iterations of the LPs with constraints are plain steps
+        if probs[p].m > 0:
+            assert all(r.branch[k - 1] == 0 for k in (40, 80, 120)), (name, p)
+    # the update changed the steps of the LPs with constraints (else the test
+    # would not see it): their trajectories part from the runs without it
+    plain = O.solve(O.OracleLP.from_problem(probs[3]), O.Params(tau=taus[3], sigma=sigs[3], **kw), iters,
+                    rec_len=iters + 1)
+    assert _rel(plain.rec_u[iters], refs[3].rec_u[iters]) > 1e-6
+    box = O.solve(O.OracleLP.from_problem(probs[5]), O.Params(tau=taus[5], sigma=sigs[5], **kw), iters,
+                  rec_len=iters + 1)
+    assert np.array_equal(box.rec_u, refs[5].rec_u)
+
+
+def _pw_solve(probs, tol):
+    with _batch(probs, "mixed") as b:
+        b.set_scaling(10, True)
+        nrm = b.estimate_norms(100, seed=1)
+        b.set_steps(0.9 / nrm, 0.9 / nrm)
+        b.set_method("aa", mem=10, D=10.0, eps=1.0)
+        b.set_primal_weight(period=500)
+        conv, its = b.iterate(200000, tol=tol, kkt_every=64)
+        return conv, b.get_iterate(), b.status()
+
+
+def test_mixed_batch_primal_weight_equals_alone_and_converges():
+    # each problem's update uses its own data only: in a batch it gets, bit
+    # for bit, the result it gets alone; every LP reaches 1e-4 by the oracle
+    probs = [lpgen.random_lp(333, 777, nnz_per_row=7, frac_ge=0.4, frac_free=0.15, frac_lower_only=0.1,
+                             frac_upper_only=0.1, row_scale_sigma=1.0, seed=4),
+             lpgen.tiny(),
+             lpgen.random_lp(120, 300, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=701)]
+    conv, got, st = _pw_solve(probs, 1e-4)
+    assert conv
+    for p, P in enumerate(probs):
+        conv1, (one,), st1 = _pw_solve([P], 1e-4)
+        assert conv1
+        assert st1[0, 0] == st[p, 0] and st1[0, 1] == st[p, 1], (p, st1[0], st[p])
+        assert np.array_equal(one[0], got[p][0]) and np.array_equal(one[1], got[p][1]), p
+        kk = O.kkt(O.OracleLP.from_problem(P), *got[p])
+        assert kk["kkt"] <= 1.05e-4, (p, kk)

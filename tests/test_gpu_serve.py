@@ -18,7 +18,7 @@ from oracle import oracle as O
 pytestmark = pytest.mark.gpu
 
 
-def _alone(P, tol, mem):
+def _alone(P, tol, mem, pw=0):
     from paper_2508_08062_gb300 import BatchSolver
     prec = "fp64" if tol < 1e-5 else "mixed"
     with BatchSolver([P], precision=prec) as b:
@@ -26,6 +26,8 @@ def _alone(P, tol, mem):
         nrm = b.estimate_norms(100, seed=1)
         b.set_steps(0.9 / nrm, 0.9 / nrm)
         b.set_method("aa", mem=mem, D=10.0, eps=1.0)
+        if pw:
+            b.set_primal_weight(period=pw)
         b.set_tolerances([tol])
         conv, _ = b.iterate(200000, tol=tol, kkt_every=64)
         (x, y), = b.get_iterate()
@@ -33,7 +35,10 @@ def _alone(P, tol, mem):
     return conv, x, y, int(st[0])
 
 
-def test_server_results_equal_alone_and_meet_their_tolerance():
+@pytest.mark.parametrize("pw", [0, 500])
+def test_server_results_equal_alone_and_meet_their_tolerance(pw):
+    # pw > 0: every cohort runs the primal weight update every pw iterations,
+    # each LP on its own, so the result alone uses the same setting
     from paper_2508_08062_gb300 import Server
     # (m, n, seed, tol): LPs the oracle takes to their tolerance (scaled as the
     # server scales them) within a few thousand AA iterations; the 1e-6 ones
@@ -46,6 +51,8 @@ def test_server_results_equal_alone_and_meet_their_tolerance():
     tols = [t for *_, t in spec]
     ids, t_sub = [], []
     with Server(method="aa", mem=5, max_cohorts=3, max_cohort_size=2, max_iters=200000) as srv:
+        if pw:
+            srv.set_primal_weight(period=pw)
         ids.append(srv.submit(probs[0], tols[0]))
         ids.append(srv.submit(probs[1], tols[1]))
         k, rounds, max_running = 2, 0, 0
@@ -66,7 +73,7 @@ def test_server_results_equal_alone_and_meet_their_tolerance():
     for P, tol, r in zip(probs, tols, res):
         assert r["state"] == "converged", r["state"]
         assert 0 <= r["t_submit"] <= r["t_admit"] <= r["t_done"]
-        conv, x, y, its = _alone(P, tol, 5)
+        conv, x, y, its = _alone(P, tol, 5, pw)
         assert conv
         assert r["iters"] == its
         assert np.array_equal(r["x"], x) and np.array_equal(r["y"], y)

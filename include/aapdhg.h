@@ -207,8 +207,12 @@ aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launc
  * (1 - alpha) diag(1/omega, omega) + alpha diag(D1/omega, D2 omega), alpha =
  * alpha_dec when the relative decrease of ||g|| over the last iteration is
  * >= rho_min, else alpha_inc (paper: alpha 0.1 / 0.9, theta 0.5, U_P 3000).
- * period = 0 switches it off.  theta, alpha_* in [0, 1], eps_zero >= 0
- * (AAPDHG_ERR_INVALID otherwise).  Resets the run.                          */
+ * period = 0 switches it off.  With FP32 iterates (AAPDHG_MIXED) and
+ * kkt_every > 0 an update is applied only while the run still improves: the
+ * last KKT test must be below every KKT seen at the earlier update points
+ * (at FP32's attainable accuracy the Deltas are rounding noise and omega
+ * would drift; FP64 applies every update, as the paper).  theta, alpha_* in
+ * [0, 1], eps_zero >= 0 (AAPDHG_ERR_INVALID otherwise).  Resets the run.    */
 aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta, double eps_zero,
                                        int32_t dhat_blend, double rho_min, double alpha_dec,
                                        double alpha_inc);

@@ -255,6 +255,7 @@ struct aapdhg_s {
     double *pw_part = nullptr;
     bool pw_base_valid = false;            // pw_dh_base holds the current base D-hat
     int64_t pw_last_k = -1;                // iterate index of the last update tried
+    double pw_best_kkt = INFINITY;         // lowest KKT seen at an update point (FP32 iterates)
     int32_t dhat_mode = -1;                // mode D-hat was last formed with
     bool scaled = false;                   // aapdhg_set_scaling applied
     std::vector<double> dr_host, dc_host;  // Dr, Dc in internal order (when scaled)
@@ -518,6 +519,7 @@ template <typename V> aapdhg_status reset_run(aapdhg_t h) {
         h->pw_gamma = sqrt(h->tau_user * h->sigma_user);
         h->pw_omega = h->tau_user > 0 ? sqrt(h->sigma_user / h->tau_user) : 1.0;
         h->pw_last_k = -1;
+        h->pw_best_kkt = INFINITY;
         if (h->pw_dh_base) {
             V *dh = const_cast<V *>(P.dh);
             if (!h->pw_base_valid) {
@@ -748,7 +750,19 @@ template <typename V> aapdhg_status pw_update(aapdhg_t h, int64_t k) {
     aapdhg_status s = read_state(h);
     if (s != AAPDHG_OK) return s;
     const double dx = sqrt(h->st_host->scratch[2]), dy = sqrt(h->st_host->scratch[3]);
-    if (!(dx > h->pw_eps && dy > h->pw_eps)) return AAPDHG_OK;
+    // FP32 iterates: an update only while the run still improves, i.e. the
+    // last KKT test is below every one seen at earlier update points.  At
+    // FP32's attainable accuracy Delta_x, Delta_y are rounding noise, and an
+    // omega driven by them drifts until sigma amplifies the FP32 error of
+    // q - Kx into y (a run diverges).  The paper works in FP64; the FP64
+    // path applies every update.
+    bool improving = true;
+    if (sizeof(V) == 4 && h->mp.kkt_every > 0 && h->st_host->kkt_valid) {
+        const double kk = h->st_host->kkt[3];
+        improving = kk < h->pw_best_kkt;
+        h->pw_best_kkt = std::min(h->pw_best_kkt, kk);
+    }
+    if (!(dx > h->pw_eps && dy > h->pw_eps) || !improving) return AAPDHG_OK;
     h->pw_omega = exp(h->pw_theta * log(dy / dx) + (1.0 - h->pw_theta) * log(h->pw_omega));
     h->mp.tau = h->pw_gamma / h->pw_omega;
     h->mp.sigma = h->pw_gamma * h->pw_omega;

@@ -88,7 +88,8 @@ struct aapdhg_batch_s {
     int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
     double tune_us[2 * NSHAPE] = {};
     // primal weight update (off when pw_period = 0): per problem gamma, omega
-    // (pw_w), the blend weight and update flag of the last try, the snapshot
+    // and the lowest KKT at an update point (pw_w), the blend weight and
+    // update flag of the last try, the snapshot
     // of u at the last update point, the base D-hat
     int64_t pw_period = 0, pw_last_g = -1;
     PwParams pw{0.5, 1e-10, 0.1, 0.1, 0.9};
@@ -366,11 +367,12 @@ template <typename V> aapdhg_status breset(bh_t h) {
         // gamma = sqrt(tau sigma) and the base D-hat (R13)
         aapdhg_status s = bupload_steps(h);
         if (s != AAPDHG_OK) return s;
-        std::vector<double> w(2 * (size_t)h->nprob);
+        std::vector<double> w(3 * (size_t)h->nprob);
         for (int32_t p = 0; p < h->nprob; ++p) {
             const double t = h->tau[p], sg = h->sigma[p];
-            w[2 * p] = t > 0 ? sqrt(t * sg) : 0.0;
-            w[2 * p + 1] = t > 0 ? sqrt(sg / t) : 1.0;
+            w[3 * p] = t > 0 ? sqrt(t * sg) : 0.0;
+            w[3 * p + 1] = t > 0 ? sqrt(sg / t) : 1.0;
+            w[3 * p + 2] = INFINITY;
         }
         BCK(h, cudaMemcpyAsync(h->pw_w, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, h->stream));
         V *dh = const_cast<V *>(P.dh);
@@ -1051,7 +1053,7 @@ aapdhg_status aapdhg_batch_set_primal_weight(aapdhg_batch_t h, int64_t period, d
             h->pw_base_valid = false;
         }
         if (!h->pw_part) h->pw_part = (double *)bdev_alloc(h, sizeof(double) * std::max(nchunk, 1));
-        if (!h->pw_w) h->pw_w = (double *)bdev_alloc(h, sizeof(double) * 2 * h->nprob);
+        if (!h->pw_w) h->pw_w = (double *)bdev_alloc(h, sizeof(double) * 3 * h->nprob);
         if (!h->pw_alpha) h->pw_alpha = (double *)bdev_alloc(h, sizeof(double) * h->nprob);
         if (!h->pw_upd) h->pw_upd = (int32_t *)bdev_alloc(h, sizeof(int32_t) * h->nprob);
         if (!h->pw_snap || !h->pw_dh_base || !h->pw_part || !h->pw_w || !h->pw_alpha || !h->pw_upd)

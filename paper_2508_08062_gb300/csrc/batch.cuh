@@ -474,7 +474,8 @@ __global__ void __launch_bounds__(BLOCK) k_mix_b(Prob<V> P, BatchView<V> B, Meth
 // host round trip:
 //   k_pw_delta_b   per chunk: sum of (u^k - snapshot)^2 (the chunk is all x
 //                  or all y), the snapshot becomes u^k (copy_only: the start);
-//   k_pw_apply_b   per problem (one thread): Delta_x, Delta_y from its chunk
+//   k_pw_apply_b   per problem (one thread; pw = gamma, omega, lowest KKT at
+//                  an update point): Delta_x, Delta_y from its chunk
 //                  sums in chunk order; when both exceed epsilon_zero the new
 //                  omega, tau = gamma / omega, sigma = gamma omega, the blend
 //                  weight alpha from rho_k of ||g^{k-1}||, ||g^{k-2}|| (R14)
@@ -518,10 +519,20 @@ __global__ void k_pw_apply_b(BatchView<V> B, const double *part, double *pw, dou
     }
     dx = sqrt(dx);
     dy = sqrt(dy);
-    if (!(dx > pp.eps_zero && dy > pp.eps_zero)) return;   // omega unchanged, no restart
-    const double gamma = pw[2 * p];
-    const double omega = exp(pp.theta * log(dy / dx) + (1.0 - pp.theta) * log(pw[2 * p + 1]));
-    pw[2 * p + 1] = omega;
+    // FP32 iterates: an update only while the problem still improves, i.e.
+    // its last KKT test is below every one seen at its earlier update points
+    // (at FP32's attainable accuracy Delta_x, Delta_y are rounding noise and
+    // an omega driven by them drifts; the FP64 path applies every update)
+    bool improving = true;
+    if (sizeof(V) == 4 && st->kkt_valid) {
+        const double kk = st->kkt[3];
+        improving = kk < pw[3 * p + 2];
+        pw[3 * p + 2] = fmin(pw[3 * p + 2], kk);
+    }
+    if (!(dx > pp.eps_zero && dy > pp.eps_zero) || !improving) return;   // omega unchanged, no restart
+    const double gamma = pw[3 * p];
+    const double omega = exp(pp.theta * log(dy / dx) + (1.0 - pp.theta) * log(pw[3 * p + 1]));
+    pw[3 * p + 1] = omega;
     const double tau = gamma / omega, sigma = gamma * omega;
     const_cast<double *>(B.tau)[p] = tau;
     const_cast<double *>(B.sigma)[p] = sigma;
@@ -539,7 +550,7 @@ __global__ void __launch_bounds__(BLOCK) k_dhat_blend_b(V *dh, const V *base, Ba
                                                         const double *alpha, const int32_t *upd) {
     const int4 ch = B.chunk[blockIdx.x];
     if (!upd[ch.x]) return;
-    const double omega = pw[2 * ch.x + 1], a = alpha[ch.x];
+    const double omega = pw[3 * ch.x + 1], a = alpha[ch.x];
     for (int64_t e = ch.y + (int64_t)threadIdx.x; e < (int64_t)ch.y + ch.z; e += BLOCK) {
         const double b = (1.0 - a) + a * (double)base[e];
         dh[e] = (V)(ch.w == 0 ? b / omega : b * omega);

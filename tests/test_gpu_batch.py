@@ -433,3 +433,10 @@ def test_mixed_batch_primal_weight_equals_alone_and_converges():
         assert np.array_equal(one[0], got[p][0]) and np.array_equal(one[1], got[p][1]), p
         kk = O.kkt(O.OracleLP.from_problem(P), *got[p])
         assert kk["kkt"] <= 1.05e-4, (p, kk)
+
+
+def test_batch_primal_weight_rejects_parameters_out_of_range():
+    from paper_2508_08062_gb300 import AAPDHGError
+    with _batch([lpgen.tiny()]) as b:
+        with pytest.raises(AAPDHGError, match="primal weight"):
+            b.set_primal_weight(period=100, theta=1.5)

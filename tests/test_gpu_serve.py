@@ -108,3 +108,18 @@ def test_server_rejects_what_cannot_fit_and_refuses_malformed_input():
             if running == 0 and waiting == 0:
                 break
         assert srv.result(b)["state"] == "converged"
+
+
+def test_server_primal_weight_rejects_parameters_out_of_range():
+    # not sticky: the server goes on with its previous setting
+    from paper_2508_08062_gb300 import AAPDHGError, Server
+    good = lpgen.random_lp(60, 150, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=700)
+    with Server(method="aa", mem=5, max_cohorts=1, max_cohort_size=1, max_iters=200000) as srv:
+        with pytest.raises(AAPDHGError, match="primal weight"):
+            srv.set_primal_weight(period=-1)
+        a = srv.submit(good, 1e-4)
+        for _ in range(20000):
+            running, waiting = srv.step()
+            if running == 0 and waiting == 0:
+                break
+        assert srv.result(a)["state"] == "converged"

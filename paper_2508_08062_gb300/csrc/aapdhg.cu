@@ -84,74 +84,140 @@ bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost 
     L.slice_meta.resize(L.n_slices);
     L.sell_ci.assign(total, 0);
     L.sell_val.assign(total, 0.0);
-    int32_t off = 0;
+    std::vector<int64_t> soff(L.n_slices + 1, 0);
     for (int32_t q = 0; q < L.n_slices; ++q) {
         const Slice &x = sl[q];
-        L.slice_meta[q] = make_int4(off, x.width, x.row0, x.rows | (x.pid << 6));
-        for (int32_t lane = 0; lane < x.rows; ++lane) {
-            const int32_t r = x.row0 + lane, lrn = len(r);
-            for (int32_t t = 0; t < lrn; ++t) {
-                const int64_t k = (int64_t)off + (int64_t)t * 32 + lane;
-                L.sell_ci[k] = A.ci[A.rp[r] + t];
-                L.sell_val[k] = A.val[A.rp[r] + t];
+        L.slice_meta[q] = make_int4((int32_t)soff[q], x.width, x.row0, x.rows | (x.pid << 6));
+        soff[q + 1] = soff[q] + 32 * (int64_t)x.width;
+    }
+    run_ranges(weight_cuts(soff.data(), L.n_slices, host_threads(total)), [&](int, int64_t lo, int64_t hi) {
+        for (int64_t q = lo; q < hi; ++q) {
+            const Slice &x = sl[q];
+            for (int32_t lane = 0; lane < x.rows; ++lane) {
+                const int32_t r = x.row0 + lane, lrn = len(r);
+                for (int32_t t = 0; t < lrn; ++t) {
+                    const int64_t k = soff[q] + (int64_t)t * 32 + lane;
+                    L.sell_ci[k] = A.ci[A.rp[r] + t];
+                    L.sell_val[k] = A.val[A.rp[r] + t];
+                }
             }
         }
-        off += 32 * x.width;
-    }
+    });
     return true;
+}
+
+int host_threads(int64_t work) {
+    if (work < ((int64_t)1 << 20)) return 1;
+    const unsigned hw = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(hw, 16u));
+}
+
+std::vector<int64_t> even_cuts(int64_t n, int T) {
+    std::vector<int64_t> cuts(T + 1);
+    for (int t = 0; t <= T; ++t) cuts[t] = n * t / T;
+    return cuts;
+}
+
+// Indices [0, N) by decreasing len, ties in index order: a counting sort, so
+// the permutation a stable sort by decreasing length gives, in linear time.
+static void order_by_length(const std::vector<int64_t> &len, std::vector<int32_t> &perm) {
+    const int64_t N = (int64_t)len.size();
+    int64_t maxl = 0;
+    for (int64_t l : len) maxl = std::max(maxl, l);
+    std::vector<int64_t> start(maxl + 2, 0);
+    for (int64_t l : len) start[maxl - l + 1]++;
+    for (int64_t b = 1; b <= maxl + 1; ++b) start[b] += start[b - 1];
+    perm.resize(N);
+    for (int64_t i = 0; i < N; ++i) perm[start[maxl - len[i]]++] = (int32_t)i;
 }
 
 void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, const double *val,
                     std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
                     HostCSR &KT) {
+    const int64_t Z = rp[m];
     std::vector<int64_t> rlen(m), clen(n, 0);
     for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
-    for (int64_t k = 0; k < rp[m]; ++k) clen[ci[k]]++;
-    perm_y.resize(m);
-    perm_x.resize(n);
-    for (int32_t i = 0; i < m; ++i) perm_y[i] = i;
-    for (int32_t j = 0; j < n; ++j) perm_x[j] = j;
-    std::stable_sort(perm_y.begin(), perm_y.end(), [&](int32_t a, int32_t b) { return rlen[a] > rlen[b]; });
-    std::stable_sort(perm_x.begin(), perm_x.end(), [&](int32_t a, int32_t b) { return clen[a] > clen[b]; });
-    std::vector<int32_t> inv_x(n), inv_y(m);
+    for (int64_t k = 0; k < Z; ++k) clen[ci[k]]++;
+    order_by_length(rlen, perm_y);
+    order_by_length(clen, perm_x);
+    std::vector<int32_t> inv_x(n);
     for (int32_t j = 0; j < n; ++j) inv_x[perm_x[j]] = j;
-    for (int32_t i = 0; i < m; ++i) inv_y[perm_y[i]] = i;
-    const int64_t Z = rp[m];
-    // K' rows (internal x) with internal y column indices: counting sort over
-    // internal x while walking internal rows in order -> ascending columns.
-    KT.rows = n;
-    KT.rp.assign(n + 1, 0);
-    for (int32_t j = 0; j < n; ++j) KT.rp[j + 1] = KT.rp[j] + (int32_t)clen[perm_x[j]];
-    KT.ci.resize(Z);
-    KT.val.resize(Z);
-    {
-        std::vector<int32_t> pos(KT.rp.begin(), KT.rp.end() - 1);
-        for (int32_t ii = 0; ii < m; ++ii) {
-            const int32_t i = perm_y[ii];
-            for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
-                const int32_t jj = inv_x[ci[k]];
-                const int32_t p = pos[jj]++;
-                KT.ci[p] = ii;
-                KT.val[p] = val[k];
-            }
-        }
-    }
-    // K rows (internal y) with internal x columns, ascending: transpose K'.
+    const int TH = host_threads(Z);
+    // K: internal row ii is the caller's row perm_y[ii], its columns in the
+    // internal order, ascending (rows in parallel)
     K.rows = m;
     K.rp.assign(m + 1, 0);
     for (int32_t ii = 0; ii < m; ++ii) K.rp[ii + 1] = K.rp[ii] + (int32_t)rlen[perm_y[ii]];
     K.ci.resize(Z);
     K.val.resize(Z);
-    {
-        std::vector<int32_t> pos(K.rp.begin(), K.rp.end() - 1);
-        for (int32_t jj = 0; jj < n; ++jj)
-            for (int32_t p = KT.rp[jj]; p < KT.rp[jj + 1]; ++p) {
-                const int32_t ii = KT.ci[p];
-                const int32_t q = pos[ii]++;
-                K.ci[q] = jj;
-                K.val[q] = KT.val[p];
+    run_ranges(weight_cuts(K.rp.data(), m, TH), [&](int, int64_t lo, int64_t hi) {
+        std::vector<std::pair<int32_t, double>> tmp;
+        for (int64_t ii = lo; ii < hi; ++ii) {
+            const int32_t i = perm_y[ii];
+            const int64_t L = rlen[i], src = rp[i];
+            int32_t *oc = K.ci.data() + K.rp[ii];
+            double *ov = K.val.data() + K.rp[ii];
+            if (L <= 32) {                                  // insertion sort in place
+                for (int64_t t = 0; t < L; ++t) {
+                    const int32_t cc = inv_x[ci[src + t]];
+                    const double vv = val[src + t];
+                    int64_t u = t;
+                    for (; u > 0 && oc[u - 1] > cc; --u) {
+                        oc[u] = oc[u - 1];
+                        ov[u] = ov[u - 1];
+                    }
+                    oc[u] = cc;
+                    ov[u] = vv;
+                }
+            } else {
+                tmp.resize(L);
+                for (int64_t t = 0; t < L; ++t) tmp[t] = {inv_x[ci[src + t]], val[src + t]};
+                std::sort(tmp.begin(), tmp.end(),
+                          [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+                              return a.first < b.first;
+                          });
+                for (int64_t t = 0; t < L; ++t) {
+                    oc[t] = tmp[t].first;
+                    ov[t] = tmp[t].second;
+                }
             }
-    }
+        }
+    });
+    // K' = K transposed.  Each thread counts the columns of a run of
+    // consecutive rows, the counts become start positions, and each thread
+    // scatters its rows in order: every K' row lists its rows ascending, as
+    // one sequential pass would.  (At most 2^27 counters in all.)
+    KT.rows = n;
+    KT.rp.assign(n + 1, 0);
+    for (int32_t jj = 0; jj < n; ++jj) KT.rp[jj + 1] = KT.rp[jj] + (int32_t)clen[perm_x[jj]];
+    KT.ci.resize(Z);
+    KT.val.resize(Z);
+    const int TT = (int)std::max<int64_t>(1, std::min<int64_t>(TH, ((int64_t)1 << 27) / std::max<int32_t>(n, 1)));
+    const std::vector<int64_t> rc = weight_cuts(K.rp.data(), m, TT);
+    std::vector<std::vector<int32_t>> cnt(TT);
+    run_ranges(rc, [&](int t, int64_t lo, int64_t hi) {
+        cnt[t].assign(n, 0);
+        for (int64_t p = K.rp[lo]; p < K.rp[hi]; ++p) cnt[t][K.ci[p]]++;
+    });
+    run_ranges(even_cuts(n, TH), [&](int, int64_t lo, int64_t hi) {
+        for (int64_t jj = lo; jj < hi; ++jj) {
+            int32_t off = KT.rp[jj];
+            for (int t = 0; t < TT; ++t) {
+                const int32_t c = cnt[t][jj];
+                cnt[t][jj] = off;
+                off += c;
+            }
+        }
+    });
+    run_ranges(rc, [&](int t, int64_t lo, int64_t hi) {
+        int32_t *pos = cnt[t].data();
+        for (int64_t ii = lo; ii < hi; ++ii)
+            for (int32_t p = K.rp[ii]; p < K.rp[ii + 1]; ++p) {
+                const int32_t q = pos[K.ci[p]]++;
+                KT.ci[q] = (int32_t)ii;
+                KT.val[q] = K.val[p];
+            }
+    });
 }
 
 std::string validate_lp(int32_t m, int32_t n, int64_t nnz, const int64_t *row_ptr,
@@ -161,20 +227,56 @@ std::string validate_lp(int32_t m, int32_t n, int64_t nnz, const int64_t *row_pt
     if (!row_ptr || (nnz > 0 && (!col_idx || !val)) || (m > 0 && (!row_sense || !q)) || !c || !lb || !ub)
         return "NULL input array";
     if (row_ptr[0] != 0 || row_ptr[m] != nnz) return "row_ptr[0] must be 0 and row_ptr[m] must be nnz";
-    std::vector<int32_t> mark(n, -1);
-    for (int32_t i = 0; i < m; ++i) {
-        if (row_ptr[i + 1] < row_ptr[i]) return "row_ptr is not non-decreasing";
-        if (row_sense[i] != AAPDHG_ROW_EQ && row_sense[i] != AAPDHG_ROW_GE)
-            return "row_sense must be 0 (=) or 1 (>=)";
-        for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            const int32_t j = col_idx[k];
-            if (j < 0 || j >= n) return "column index out of range";
-            if (mark[j] == i) return "repeated column within a row";
-            mark[j] = i;
+    // the rows before the first one whose pointer decreases (or leaves
+    // [0, nnz]) are read; each row's checks run in order, and the error
+    // reported is that of the first failing row
+    int32_t r_bad = m;
+    for (int32_t i = 0; i < m; ++i)
+        if (row_ptr[i + 1] < row_ptr[i] || row_ptr[i + 1] > nnz) {
+            r_bad = i;
+            break;
         }
-    }
-    for (int64_t k = 0; k < nnz; ++k)
-        if (!std::isfinite(val[k])) return "non-finite value in K, q or c";
+    const int TH = host_threads(nnz);
+    const int TT = (int)std::max<int64_t>(1, std::min<int64_t>(TH, ((int64_t)1 << 27) / n));   // marks
+    const std::vector<int64_t> cuts = weight_cuts(row_ptr, r_bad, TT);
+    std::vector<int32_t> bad_row(TT, INT32_MAX);
+    std::vector<const char *> bad_msg(TT, nullptr);
+    run_ranges(cuts, [&](int t, int64_t lo, int64_t hi) {
+        std::vector<int32_t> mark(n, -1);
+        for (int64_t i = lo; i < hi; ++i) {
+            const char *msg = nullptr;
+            if (row_sense[i] != AAPDHG_ROW_EQ && row_sense[i] != AAPDHG_ROW_GE) {
+                msg = "row_sense must be 0 (=) or 1 (>=)";
+            } else {
+                for (int64_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                    const int32_t j = col_idx[k];
+                    if (j < 0 || j >= n) { msg = "column index out of range"; break; }
+                    if (mark[j] == (int32_t)i) { msg = "repeated column within a row"; break; }
+                    mark[j] = (int32_t)i;
+                }
+            }
+            if (msg) {
+                bad_row[t] = (int32_t)i;
+                bad_msg[t] = msg;
+                return;
+            }
+        }
+    });
+    int tb = 0;
+    for (int t = 1; t < TT; ++t)
+        if (bad_row[t] < bad_row[tb]) tb = t;
+    if (bad_msg[tb]) return bad_msg[tb];
+    if (r_bad < m) return "row_ptr is not non-decreasing";
+    std::vector<char> nonfinite(TH, 0);
+    run_ranges(even_cuts(nnz, TH), [&](int t, int64_t lo, int64_t hi) {
+        for (int64_t k = lo; k < hi; ++k)
+            if (!std::isfinite(val[k])) {
+                nonfinite[t] = 1;
+                return;
+            }
+    });
+    for (char f : nonfinite)
+        if (f) return "non-finite value in K, q or c";
     for (int32_t i = 0; i < m; ++i)
         if (!std::isfinite(q[i])) return "non-finite value in K, q or c";
     for (int32_t j = 0; j < n; ++j)

@@ -843,12 +843,31 @@ aapdhg_status aapdhg_batch_create(int32_t nprob, const int32_t *m, const int32_t
     }
     if (Z >= ((int64_t)1 << 31) || xt + yt >= ((int64_t)1 << 31))
         return bfail(nullptr, AAPDHG_ERR_INVALID, "the packed batch needs < 2^31 nonzeros and elements");
-    for (int32_t p = 0; p < nprob; ++p) {
-        const std::string why = validate_lp(
-            m[p], n[p], nnz[p], row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
-            nnz[p] ? val + kc[p] : nullptr, m[p] ? row_sense + yc[p] : nullptr, m[p] ? q + yc[p] : nullptr,
-            c ? c + xc[p] : nullptr, lb ? lb + xc[p] : nullptr, ub ? ub + xc[p] : nullptr);
-        if (!why.empty()) return bfail(nullptr, AAPDHG_ERR_INVALID, "problem " + std::to_string(p) + ": " + why);
+    // problems checked in parallel (weighted by nonzeros); the lowest failing one is reported
+    std::vector<int64_t> zpre(nprob + 1, 0);
+    for (int32_t p = 0; p < nprob; ++p) zpre[p + 1] = zpre[p] + nnz[p] + m[p] + n[p];
+    const std::vector<int64_t> pcuts = weight_cuts(zpre.data(), nprob, host_threads(zpre[nprob]));
+    std::vector<int32_t> bad_p(pcuts.size() - 1, nprob);
+    std::vector<std::string> bad_why(pcuts.size() - 1);
+    run_ranges(pcuts, [&](int t, int64_t lo, int64_t hi) {
+        for (int64_t p = lo; p < hi; ++p) {
+            std::string why = validate_lp(
+                m[p], n[p], nnz[p], row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
+                nnz[p] ? val + kc[p] : nullptr, m[p] ? row_sense + yc[p] : nullptr, m[p] ? q + yc[p] : nullptr,
+                c ? c + xc[p] : nullptr, lb ? lb + xc[p] : nullptr, ub ? ub + xc[p] : nullptr);
+            if (!why.empty()) {
+                bad_p[t] = (int32_t)p;
+                bad_why[t] = std::move(why);
+                return;
+            }
+        }
+    });
+    {
+        size_t tb = 0;
+        for (size_t t = 1; t < bad_p.size(); ++t)
+            if (bad_p[t] < bad_p[tb]) tb = t;
+        if (bad_p[tb] < nprob)
+            return bfail(nullptr, AAPDHG_ERR_INVALID, "problem " + std::to_string(bad_p[tb]) + ": " + bad_why[tb]);
     }
 
     bh_t h = new (std::nothrow) aapdhg_batch_s();
@@ -892,67 +911,69 @@ aapdhg_status aapdhg_batch_create(int32_t nprob, const int32_t *m, const int32_t
     h->tau.assign(nprob, 0.0);
     h->sigma.assign(nprob, 0.0);
 
-    // per-problem renumbering, packed into one K and one K'
+    // per-problem renumbering, packed into one K and one K': problem p's
+    // nonzeros occupy [kc[p], kc[p] + nnz[p]) of both, so the problems are
+    // renumbered in parallel (weighted by nonzeros) and written in place
     HostCSR K, KT;
     K.rows = (int32_t)h->m_tot;
     KT.rows = (int32_t)h->n_tot;
     K.rp.assign(h->m_tot + 1, 0);
     KT.rp.assign(h->n_tot + 1, 0);
-    K.ci.reserve(Z); K.val.reserve(Z); KT.ci.reserve(Z); KT.val.reserve(Z);
+    K.ci.resize(Z); K.val.resize(Z); KT.ci.resize(Z); KT.val.resize(Z);
     std::vector<double> cv(h->n_tot, 0.0), qv(std::max<int64_t>(h->m_tot, 1), 0.0);
     std::vector<double> lov(h->N, 0.0), hiv(h->N, 0.0), pnorm(2 * (size_t)nprob);
     std::vector<RowSeg> segK, segKT;
-    h->perm_x.reserve(X);
-    h->perm_y.reserve(Y);
     for (int32_t p = 0; p < nprob; ++p) {
-        std::vector<int32_t> px, py;
-        HostCSR Kp, KTp;
-        const int32_t mp_ = m[p], np_ = n[p];
-        build_internal(mp_, np_, row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
-                       nnz[p] ? val + kc[p] : nullptr, px, py, Kp, KTp);
-        const int64_t xo = h->xoff[p], yo = h->yoff[p];
-        for (int32_t ii = 0; ii < h->nyp[p]; ++ii) {
-            if (ii < mp_)
-                for (int32_t k = Kp.rp[ii]; k < Kp.rp[ii + 1]; ++k) {
-                    K.ci.push_back((int32_t)(xo + Kp.ci[k]));
-                    K.val.push_back(Kp.val[k]);
-                }
-            K.rp[yo + ii + 1] = (int32_t)K.ci.size();
-        }
-        for (int32_t jj = 0; jj < h->nxp[p]; ++jj) {
-            if (jj < np_)
-                for (int32_t k = KTp.rp[jj]; k < KTp.rp[jj + 1]; ++k) {
-                    KT.ci.push_back((int32_t)(yo + KTp.ci[k]));
-                    KT.val.push_back(KTp.val[k]);
-                }
-            KT.rp[xo + jj + 1] = (int32_t)KT.ci.size();
-        }
-        segK.push_back(RowSeg{(int32_t)yo, h->nyp[p], p});
-        segKT.push_back(RowSeg{(int32_t)xo, h->nxp[p], p});
-        double q2 = 0.0, c2 = 0.0;
-        for (int32_t j = 0; j < np_; ++j) {
-            const int64_t oj = xc[p] + px[j];
-            cv[xo + j] = c[oj];
-            lov[xo + j] = lb[oj];
-            hiv[xo + j] = ub[oj];
-            c2 += c[oj] * c[oj];
-        }
-        for (int32_t i = 0; i < h->nyp[p]; ++i) {
-            const int64_t e2 = h->n_tot + yo + i;
-            hiv[e2] = INFINITY;
-            lov[e2] = -INFINITY;
-            if (i < mp_) {
-                const int64_t oi = yc[p] + py[i];
-                qv[yo + i] = q[oi];
-                lov[e2] = row_sense[oi] == AAPDHG_ROW_GE ? 0.0 : -INFINITY;
-                q2 += q[oi] * q[oi];
-            }
-        }
-        pnorm[2 * p] = sqrt(q2);
-        pnorm[2 * p + 1] = sqrt(c2);
-        h->perm_x.insert(h->perm_x.end(), px.begin(), px.end());
-        h->perm_y.insert(h->perm_y.end(), py.begin(), py.end());
+        segK.push_back(RowSeg{(int32_t)h->yoff[p], h->nyp[p], p});
+        segKT.push_back(RowSeg{(int32_t)h->xoff[p], h->nxp[p], p});
     }
+    h->perm_x.resize(X);
+    h->perm_y.resize(Y);
+    run_ranges(pcuts, [&](int, int64_t lo, int64_t hi) {
+        for (int64_t p = lo; p < hi; ++p) {
+            std::vector<int32_t> px, py;
+            HostCSR Kp, KTp;
+            const int32_t mp_ = m[p], np_ = n[p];
+            build_internal(mp_, np_, row_ptr + rpc[p], nnz[p] ? col_idx + kc[p] : nullptr,
+                           nnz[p] ? val + kc[p] : nullptr, px, py, Kp, KTp);
+            const int64_t xo = h->xoff[p], yo = h->yoff[p], z0 = kc[p];
+            for (int32_t ii = 0; ii < h->nyp[p]; ++ii)
+                K.rp[yo + ii + 1] = (int32_t)(z0 + (ii < mp_ ? Kp.rp[ii + 1] : nnz[p]));
+            for (int64_t k = 0; k < nnz[p]; ++k) {
+                K.ci[z0 + k] = (int32_t)(xo + Kp.ci[k]);
+                K.val[z0 + k] = Kp.val[k];
+            }
+            for (int32_t jj = 0; jj < h->nxp[p]; ++jj)
+                KT.rp[xo + jj + 1] = (int32_t)(z0 + (jj < np_ ? KTp.rp[jj + 1] : nnz[p]));
+            for (int64_t k = 0; k < nnz[p]; ++k) {
+                KT.ci[z0 + k] = (int32_t)(yo + KTp.ci[k]);
+                KT.val[z0 + k] = KTp.val[k];
+            }
+            double q2 = 0.0, c2 = 0.0;
+            for (int32_t j = 0; j < np_; ++j) {
+                const int64_t oj = xc[p] + px[j];
+                cv[xo + j] = c[oj];
+                lov[xo + j] = lb[oj];
+                hiv[xo + j] = ub[oj];
+                c2 += c[oj] * c[oj];
+            }
+            for (int32_t i = 0; i < h->nyp[p]; ++i) {
+                const int64_t e2 = h->n_tot + yo + i;
+                hiv[e2] = INFINITY;
+                lov[e2] = -INFINITY;
+                if (i < mp_) {
+                    const int64_t oi = yc[p] + py[i];
+                    qv[yo + i] = q[oi];
+                    lov[e2] = row_sense[oi] == AAPDHG_ROW_GE ? 0.0 : -INFINITY;
+                    q2 += q[oi] * q[oi];
+                }
+            }
+            pnorm[2 * p] = sqrt(q2);
+            pnorm[2 * p + 1] = sqrt(c2);
+            std::copy(px.begin(), px.end(), h->perm_x.begin() + xc[p]);
+            std::copy(py.begin(), py.end(), h->perm_y.begin() + yc[p]);
+        }
+    });
     qv.resize(std::max<int64_t>(h->m_tot, 1));
     aapdhg_status s = precision == AAPDHG_FP64
                           ? bsetup<double>(h, K, KT, segK, segKT, cv, qv, lov, hiv, pnorm)

@@ -7,11 +7,55 @@
 #include <algorithm>
 #include <cstdint>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "common.cuh"
 
 namespace aaph {
+
+// Host threads for the set-up work of one LP with `work` entries: 1 below
+// 2^20 (thread start-up would dominate), else the hardware's, at most 16.
+int host_threads(int64_t work);
+
+// T + 1 ascending cuts of [0, n): equal counts, or equal weight under the
+// partial sums prefix[0..n] (a CSR row pointer).
+std::vector<int64_t> even_cuts(int64_t n, int T);
+template <typename P> std::vector<int64_t> weight_cuts(const P *prefix, int64_t n, int T) {
+    std::vector<int64_t> cuts(T + 1, n);
+    cuts[0] = 0;
+    const double p0 = (double)prefix[0], tot = (double)prefix[n] - p0;
+    for (int t = 1; t < T; ++t) {
+        const double target = p0 + tot * t / T;
+        int64_t lo = cuts[t - 1], hi = n;              // first i with prefix[i] >= target
+        while (lo < hi) {
+            const int64_t mid = lo + (hi - lo) / 2;
+            if ((double)prefix[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        cuts[t] = lo;
+    }
+    return cuts;
+}
+
+// f(t, lo, hi) for every range t of `cuts`, on one thread each (the calling
+// thread takes range 0; a thread that cannot be started runs its range on
+// the calling thread).  Each call must write only its own range's outputs.
+template <class F> void run_ranges(const std::vector<int64_t> &cuts, F &&f) {
+    const int T = (int)cuts.size() - 1;
+    std::vector<std::thread> th;
+    std::vector<int> inline_t;
+    for (int t = 1; t < T; ++t) {
+        try {
+            th.emplace_back([&f, &cuts, t] { f(t, cuts[t], cuts[t + 1]); });
+        } catch (...) {
+            inline_t.push_back(t);
+        }
+    }
+    if (T >= 1) f(0, cuts[0], cuts[1]);
+    for (int t : inline_t) f(t, cuts[t], cuts[t + 1]);
+    for (auto &x : th) x.join();
+}
 
 struct HostCSR {
     int32_t rows = 0;
@@ -76,7 +120,10 @@ bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Al
     };
     auto to_v = [](const std::vector<double> &a) {
         std::vector<V> o(a.size());
-        for (size_t i = 0; i < a.size(); ++i) o[i] = (V)a[i];
+        run_ranges(even_cuts((int64_t)a.size(), host_threads((int64_t)a.size())),
+                   [&](int, int64_t lo, int64_t hi) {
+                       for (int64_t i = lo; i < hi; ++i) o[i] = (V)a[i];
+                   });
         return o;
     };
     view.rows = A.rows;

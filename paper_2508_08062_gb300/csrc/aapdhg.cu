@@ -135,14 +135,28 @@ void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, 
                     std::vector<int32_t> &perm_x, std::vector<int32_t> &perm_y, HostCSR &K,
                     HostCSR &KT) {
     const int64_t Z = rp[m];
-    std::vector<int64_t> rlen(m), clen(n, 0);
+    const int TH = host_threads(Z);
+    // per-thread column counters over runs of consecutive rows (at most 2^27
+    // counters in all): the column degrees here, the transpose below
+    const int TT = (int)std::max<int64_t>(1, std::min<int64_t>(TH, ((int64_t)1 << 27) / std::max<int32_t>(n, 1)));
+    std::vector<std::vector<int32_t>> cnt(TT);
+    std::vector<int64_t> rlen(m), clen(n);
     for (int32_t i = 0; i < m; ++i) rlen[i] = rp[i + 1] - rp[i];
-    for (int64_t k = 0; k < Z; ++k) clen[ci[k]]++;
+    run_ranges(weight_cuts(rp, m, TT), [&](int t, int64_t lo, int64_t hi) {
+        cnt[t].assign(n, 0);
+        for (int64_t k = rp[lo]; k < rp[hi]; ++k) cnt[t][ci[k]]++;
+    });
+    run_ranges(even_cuts(n, TH), [&](int, int64_t lo, int64_t hi) {
+        for (int64_t j = lo; j < hi; ++j) {
+            int64_t d = 0;
+            for (int t = 0; t < TT; ++t) d += cnt[t][j];
+            clen[j] = d;
+        }
+    });
     order_by_length(rlen, perm_y);
     order_by_length(clen, perm_x);
     std::vector<int32_t> inv_x(n);
     for (int32_t j = 0; j < n; ++j) inv_x[perm_x[j]] = j;
-    const int TH = host_threads(Z);
     // K: internal row ii is the caller's row perm_y[ii], its columns in the
     // internal order, ascending (rows in parallel)
     K.rows = m;
@@ -186,17 +200,15 @@ void build_internal(int32_t m, int32_t n, const int64_t *rp, const int32_t *ci, 
     // K' = K transposed.  Each thread counts the columns of a run of
     // consecutive rows, the counts become start positions, and each thread
     // scatters its rows in order: every K' row lists its rows ascending, as
-    // one sequential pass would.  (At most 2^27 counters in all.)
+    // one sequential pass would.
     KT.rows = n;
     KT.rp.assign(n + 1, 0);
     for (int32_t jj = 0; jj < n; ++jj) KT.rp[jj + 1] = KT.rp[jj] + (int32_t)clen[perm_x[jj]];
     KT.ci.resize(Z);
     KT.val.resize(Z);
-    const int TT = (int)std::max<int64_t>(1, std::min<int64_t>(TH, ((int64_t)1 << 27) / std::max<int32_t>(n, 1)));
     const std::vector<int64_t> rc = weight_cuts(K.rp.data(), m, TT);
-    std::vector<std::vector<int32_t>> cnt(TT);
     run_ranges(rc, [&](int t, int64_t lo, int64_t hi) {
-        cnt[t].assign(n, 0);
+        std::fill(cnt[t].begin(), cnt[t].end(), 0);
         for (int64_t p = K.rp[lo]; p < K.rp[hi]; ++p) cnt[t][K.ci[p]]++;
     });
     run_ranges(even_cuts(n, TH), [&](int, int64_t lo, int64_t hi) {

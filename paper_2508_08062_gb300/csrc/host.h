@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <string>
 #include <thread>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -57,10 +58,22 @@ template <class F> void run_ranges(const std::vector<int64_t> &cuts, F &&f) {
     for (auto &x : th) x.join();
 }
 
+// An allocator whose value-less construction leaves trivial types
+// uninitialised: a large host array sized with resize() is first touched by
+// the threads that fill it, not zeroed by one thread beforehand.
+template <class T> struct uninit_alloc : std::allocator<T> {
+    template <class U> struct rebind { typedef uninit_alloc<U> other; };
+    uninit_alloc() = default;
+    template <class U> uninit_alloc(const uninit_alloc<U> &) noexcept {}
+    template <class U> void construct(U *p) noexcept { ::new ((void *)p) U; }
+    template <class U, class... A> void construct(U *p, A &&...a) { ::new ((void *)p) U(std::forward<A>(a)...); }
+};
+template <class T> using hvec = std::vector<T, uninit_alloc<T>>;
+
 struct HostCSR {
     int32_t rows = 0;
-    std::vector<int32_t> rp, ci;
-    std::vector<double> val;
+    hvec<int32_t> rp, ci;         // every entry written after resize()
+    hvec<double> val;
 };
 
 // Rows [row0, row0 + rows) of one problem, sorted longest first.
@@ -118,7 +131,7 @@ bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Al
             ok = false;
         return d;
     };
-    auto to_v = [](const std::vector<double> &a) {
+    auto to_v = [](const auto &a) {
         std::vector<V> o(a.size());
         run_ranges(even_cuts((int64_t)a.size(), host_threads((int64_t)a.size())),
                    [&](int, int64_t lo, int64_t hi) {

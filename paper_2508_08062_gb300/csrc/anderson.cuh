@@ -352,7 +352,7 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     __shared__ int s_old[NSLOT];
     __shared__ int64_t s_off[NSLOT];
     __shared__ int s_nold, s_new, s_prev_acc;
-    __shared__ double sh[WARPS * (MC + 3)];
+    __shared__ typename Acc<V>::Packed sh[WARPS * (MC + 3)];
     const int cur = (mode == MODE_INIT) ? 0 : (int)(st->it & 1) ^ 1;
     // the iteration of a primal weight update restarts the memory: a plain
     // step, g^k kept as the previous residual, no column formed across it
@@ -422,14 +422,14 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
         for (int s = 0; s < MC + 3; ++s) {
             if (s < nold || s >= MC) {
                 acc[s].warp_allreduce();
-                if (lane == 0) sh[warp * (MC + 3) + s] = acc[s].value();
+                if (lane == 0) sh[warp * (MC + 3) + s] = acc[s].pack();
             }
         }
         __syncthreads();
         for (int s = threadIdx.x; s < MC + 3; s += BLOCK) {
             if (s < nold || s >= MC) {
                 double v = 0.0;
-                for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 3) + s];
+                for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * (MC + 3) + s]);
                 P.part3[(int64_t)blockIdx.x * (MC + 3) + s] = v;
             }
         }

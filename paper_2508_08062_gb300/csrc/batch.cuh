@@ -279,7 +279,7 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     const bool fresh = init || restart || M == 0;   // only g^k and ||g^k||^2
     __shared__ int64_t s_off[NSLOT];
     __shared__ int s_nold, s_new, s_prev_acc;
-    __shared__ double sh[WARPS * (MC + 4)];
+    __shared__ typename Acc<V>::Packed sh[WARPS * (MC + 4)];
     if (threadIdx.x == 0) {
         const int cnt = fresh ? 0 : st->count;
         const int drop = (cnt == M) ? 1 : 0;
@@ -329,14 +329,14 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     for (int k = 0; k < MC + 4; ++k) {
         if (k < nold || k >= MC) {
             acc[k].warp_allreduce();
-            if (lane == 0) sh[warp * (MC + 4) + k] = acc[k].value();
+            if (lane == 0) sh[warp * (MC + 4) + k] = acc[k].pack();
         }
     }
     __syncthreads();
     for (int k = threadIdx.x; k < MC + 4; k += BLOCK) {
         if (k < nold || k >= MC) {
             double v = 0.0;
-            for (int w = 0; w < WARPS; ++w) v += sh[w * (MC + 4) + k];
+            for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * (MC + 4) + k]);
             B.cpart[(int64_t)blockIdx.x * NBV + (k < MC ? k : MAXM + (k - MC))] = v;
         }
     }

@@ -52,6 +52,10 @@ template <> struct Acc<double> {
         for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     }
     __device__ __forceinline__ double value() const { return s; }
+    // a warp's partial parked in shared memory, read back as value() would give it
+    typedef double Packed;
+    __device__ __forceinline__ Packed pack() const { return s; }
+    static __device__ __forceinline__ double unpack(Packed p) { return p; }
 };
 
 template <> struct Acc<float> {
@@ -82,6 +86,11 @@ template <> struct Acc<float> {
         }
     }
     __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+    // a warp's partial parked in shared memory as the float pair: the FP64
+    // conversion is left to the one lane per column that sums the warps
+    typedef float2 Packed;
+    __device__ __forceinline__ Packed pack() const { return make_float2(hi, lo); }
+    static __device__ __forceinline__ double unpack(Packed p) { return (double)p.x + (double)p.y; }
 };
 
 template <typename V> struct Vec2;

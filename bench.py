@@ -276,6 +276,7 @@ def run_ours(args):
     tot = sum(d["total_ms"] for d in prof.values())
     for kind in kern:
         kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
+        kern[kind]["traffic"] = committed_traffic(args.workload, kind, args.scale)
     dom = max(kern, key=lambda k: prof[k]["total_ms"])
     traffic = committed_traffic(args.workload, dom, args.scale)
     roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
@@ -635,6 +636,7 @@ def run_batch(args):
     tot = sum(d["total_ms"] for d in prof.values())
     for kind in kern:
         kern[kind]["share"] = prof[kind]["total_ms"] / tot if tot else None
+        kern[kind]["traffic"] = committed_traffic("batch", kind, args.scale)
     dom = max((k for k in kern if kern[k]["gbs"]), key=lambda k: prof[k]["total_ms"])
     roofline = {"bound": "hbm", "achieved": kern[dom]["gbs"], "peak": peak, "unit": "GB/s",
                 "frac": kern[dom]["frac_of_measured_hbm"], "kernel": dom,

@@ -88,6 +88,17 @@ def max_over_ranks(x, world, device="cuda"):
     return float(t.item())
 
 
+def sum_over_ranks(x, world, device="cuda"):
+    """The ranks' values summed (units that differ between ranks, e.g. LPs solved)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def whole_job_rate(world, units_per_rank, t_max_ms):
     """Units of all ranks per second of the slowest rank (replicas: weak scaling)."""
     return world * units_per_rank / (t_max_ms / 1e3)
@@ -592,7 +603,8 @@ def run_batch(args):
     st = b.status()
     solved = int(st[:, 4].sum())
     t_max = max_over_ranks(ms, world)
-    value = whole_job_rate(world, solved, t_max)
+    # each rank solves its own batch: the LPs all ranks solved over the slowest rank's time
+    value = sum_over_ranks(solved, world) / (t_max / 1e3)
     kk = b.get_kkt()
 
     # throughput with every member active (tol = 0) and the roofline
@@ -654,8 +666,8 @@ def run_batch(args):
         solved2 = int(b2.status()[:, 4].sum())
         b2.get_iterate()
     barrier()
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * solved2 / e2e_s, "unit": "solves/s",
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world)
+    e2e = {"value": sum_over_ranks(solved2, world) / e2e_s, "unit": "solves/s",
            "h2d_bytes_per_step": sum(problem_bytes(P) for P in members) / max(its2, 1),
            "d2h_bytes_per_step": (8 * sum(P.n + P.m for P in members)) / max(its2, 1),
            "session": "create from host CSR of 256 LPs (validation, renumbering, packing, H2D) "
@@ -743,8 +755,11 @@ def run_serve(args):
     import lpgen
     from paper_2508_08062_gb300 import Server, Solver
 
+    import torch.distributed as dist
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     wl = WORKLOADS["serve"]
     M = wl["mem"]
     rng = np.random.default_rng(lpgen.SEED_BASE + 5 + 1000 * rank)
@@ -789,7 +804,8 @@ def run_serve(args):
     for tv in (1e-4, 1e-6):
         sel = [r for r, t in zip(res, tols[:len(res)]) if t == tv and r["state"] == "converged"]
         per_tol[str(tv)] = len(sel)
-    value = len(done) / wall
+    # each rank serves its own stream: all ranks' solves over the slowest rank's wall time
+    value = sum_over_ranks(len(done), world) / max_over_ranks(wall, world)
 
     # FIFO replay through the FP64 single-LP solver: service time per
     # (instance, tolerance) measured on a sample of the pool
@@ -856,7 +872,10 @@ def run_serve(args):
                 "session": "every request from host arrays through the public server API, "
                            "results read back: the value is already end to end"},
     }
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def cpu_baseline_batch(members, st, M, budget_s=20.0, pw_period=0):

@@ -565,6 +565,21 @@ def test_pock_chambolle_by_hand():
     assert np.allclose(dc, [1 / np.sqrt(5), 1 / 3], rtol=1e-15)
 
 
+def test_one_ruiz_pass_by_hand():
+    # K = [[4, 1], [0, 9]]: row maxima 4, 9 and column maxima 4, 9 of the same
+    # matrix give D_r = D_c = (1/2, 1/3).  (Taking the column maxima from the
+    # row-scaled matrix would give D_c = (1/sqrt 2, 1/sqrt 3).)
+    P = lpgen.from_dense([[4.0, 1.0], [0.0, 9.0]], [0, 0], [1, 1], [1, 1], [0, 0], [1, 1])
+    dr, dc = O.scaling(O.OracleLP.from_problem(P), 1, False)
+    assert np.allclose(dr, [0.5, 1 / 3], rtol=1e-15)
+    assert np.allclose(dc, [0.5, 1 / 3], rtol=1e-15)
+    # an empty row or column keeps the factor 1
+    Q = lpgen.from_dense([[4.0, 0.0], [0.0, 0.0]], [0, 0], [1, 1], [1, 1], [0, 0], [1, 1])
+    dr, dc = O.scaling(O.OracleLP.from_problem(Q), 3, False)
+    assert np.allclose(dr, [0.5, 1.0], rtol=1e-15)
+    assert np.allclose(dc, [0.5, 1.0], rtol=1e-15)
+
+
 def test_ruiz_equilibrates_inf_norms():
     P = lpgen.random_lp(60, 90, nnz_per_row=6, row_scale_sigma=3.0, seed=4)
     lp = O.OracleLP.from_problem(P)

@@ -322,6 +322,23 @@ int orc_aa_coeffs(int64_t N, int32_t k, const double *dG, const double *g, doubl
     return rc;
 }
 
+/* The Anderson step before the projection (Alg. 2, AA branch):
+ *     u_AA = u^k - H^k g^k,   H^k = -beta D-hat + (dU + beta D-hat dG) (dG'dG + eta I)^-1 dG',
+ * so with gamma = (dG'dG + eta I)^-1 dG'g^k (orc_aa_coeffs, or the FAA solve)
+ *     u_AA = u^k + beta D-hat g^k - (dU + beta D-hat dG) gamma.
+ * E = dU and F = dG are N x k column-major; dh is the diagonal of D-hat.
+ * The projection P onto X x Y is applied by the caller.                      */
+void orc_aa_mix(int64_t N, int32_t k, const double *u, const double *g, const double *E,
+                const double *F, const double *dh, double beta, const double *gamma,
+                double *out) {
+    for (int64_t e = 0; e < N; ++e) {
+        double s = 0.0;
+        for (int j = 0; j < k; ++j)
+            s += (E[(int64_t)j * N + e] + beta * dh[e] * F[(int64_t)j * N + e]) * gamma[j];
+        out[e] = u[e] + beta * dh[e] * g[e] - s;
+    }
+}
+
 /* Economy QR by Householder reflections of an N x k column-major matrix F.
  * On return R (k x k, row-major, upper triangular) holds the R factor and, if
  * qtb is given, qtb = Q' b for the vector b.  Signs of R's rows follow the
@@ -593,14 +610,8 @@ int orc_solve(const orc_lp *lp, const orc_params *p, const double *x0, const dou
                 }
             }
             if (rc == 0) {
-                /* u_AA = u^k - H^k g^k
-                 *      = u^k + beta D g^k - (dU + beta D dG) gamma, then P */
-                for (int64_t e = 0; e < N; ++e) {
-                    double s = 0.0;
-                    for (int j = 0; j < kc; ++j)
-                        s += (Eu[(int64_t)j * N + e] + p->beta * dh[e] * Fg[(int64_t)j * N + e]) * gam[j];
-                    uh[e] = u[e] + p->beta * dh[e] * g[e] - s;   /* uh reused as u_AA */
-                }
+                /* u^{k+1} = P(u^k - H^k g^k); uh is reused for u_AA */
+                orc_aa_mix(N, kc, u, g, Eu, Fg, dh, p->beta, gam, uh);
                 project(lp, uh, uh + n);
                 branch = 1; used = kc;
             } else {

@@ -60,6 +60,7 @@ def lib():
         L.orc_kkt.argtypes = [vp, vp, vp, vp]
         L.orc_aa_coeffs.argtypes = [C.c_int64, C.c_int32, vp, vp, C.c_double, vp]
         L.orc_aa_coeffs.restype = C.c_int
+        L.orc_aa_mix.argtypes = [C.c_int64, C.c_int32, vp, vp, vp, vp, vp, C.c_double, vp, vp]
         L.orc_qr_coeffs.argtypes = [C.c_int64, C.c_int32, vp, vp, vp]
         L.orc_qr_coeffs.restype = C.c_int
         L.orc_length_bounds.argtypes = [C.c_int32, vp, C.c_double, vp]
@@ -178,6 +179,20 @@ def aa_coeffs(dG, g, eta):
     gam = np.zeros(k)
     rc = lib().orc_aa_coeffs(N, k, _p(F), _p(g), eta, _p(gam))
     return rc, gam
+
+
+def aa_mix(u, g, dU, dG, dhat, beta, gamma):
+    """u + beta D-hat g - (dU + beta D-hat dG) gamma (the AA step of Alg. 2
+    before the projection); dU, dG are (N, k)."""
+    N, k = dG.shape
+    E = np.ascontiguousarray(dU.T, dtype=np.float64)
+    F = np.ascontiguousarray(dG.T, dtype=np.float64)
+    u = np.ascontiguousarray(u, dtype=np.float64); g = np.ascontiguousarray(g, dtype=np.float64)
+    dh = np.ascontiguousarray(dhat, dtype=np.float64)
+    gam = np.ascontiguousarray(gamma, dtype=np.float64)
+    out = np.empty(N)
+    lib().orc_aa_mix(N, k, _p(u), _p(g), _p(E), _p(F), _p(dh), float(beta), _p(gam), _p(out))
+    return out
 
 
 def qr_coeffs(dG, g):

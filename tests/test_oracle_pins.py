@@ -341,6 +341,100 @@ def test_aa_step_equals_alg1():
 
 
 # --------------------------------------------------------------------------
+# Where D-hat and beta enter the AA step (Alg. 2, the H-form H^k).  With
+# H^k = -beta D-hat + (dU + beta D-hat dG)(dG'dG)^-1 dG' (eta = 0):
+#   H^k dG = dU           (multi-secant: no D-hat, no beta)
+#   H^k r  = -beta D-hat r for r orthogonal to span(dG).
+# Both hold for any diagonal D-hat and any beta, so a D-hat placed on dU
+# instead of dG, or a beta dropped from either term, breaks one of them.
+# --------------------------------------------------------------------------
+def _mix_case(seed, N=40, k=4):
+    rng = np.random.default_rng(seed)
+    dU = rng.standard_normal((N, k))
+    dG = rng.standard_normal((N, k))
+    dh = rng.uniform(0.3, 3.0, N)            # a diagonal D-hat far from I
+    u = rng.standard_normal(N)
+    return rng, dU, dG, dh, u
+
+
+def _orth_to(dG, r):
+    Q, _ = np.linalg.qr(dG)
+    return r - Q @ (Q.T @ r)
+
+
+def test_aa_mix_multisecant_with_dhat_and_beta():
+    for seed in range(5):
+        rng, dU, dG, dh, u = _mix_case(seed)
+        w = rng.standard_normal(dG.shape[1])
+        g = dG @ w                             # g^k in span(dG)
+        rc, gam = O.aa_coeffs(dG, g, 0.0)
+        assert rc == 0 and np.allclose(gam, w, rtol=0, atol=1e-11)
+        for beta in (0.5, 0.25, 1.0):
+            step = O.aa_mix(u, g, dU, dG, dh, beta, gam)
+            assert np.allclose(step, u - dU @ w, rtol=0, atol=1e-10), (seed, beta)
+
+
+def test_aa_mix_residual_orthogonal_to_history():
+    for seed in range(5):
+        rng, dU, dG, dh, u = _mix_case(seed)
+        g = _orth_to(dG, rng.standard_normal(dG.shape[0]))
+        rc, gam = O.aa_coeffs(dG, g, 0.0)
+        assert rc == 0 and np.max(np.abs(gam)) < 1e-12
+        for beta in (0.5, 0.25, 1.0):
+            step = O.aa_mix(u, g, dU, dG, dh, beta, gam)
+            assert np.allclose(step, u + beta * dh * g, rtol=0, atol=1e-12), (seed, beta)
+
+
+def test_aa_mix_general_residual():
+    # g = dG w + r with r orthogonal to span(dG): u - H g = u - dU w + beta D-hat r
+    for seed in range(5):
+        rng, dU, dG, dh, u = _mix_case(seed, N=60, k=6)
+        w = rng.standard_normal(dG.shape[1])
+        r = _orth_to(dG, rng.standard_normal(dG.shape[0]))
+        g = dG @ w + r
+        rc, gam = O.aa_coeffs(dG, g, 0.0)
+        assert rc == 0
+        step = O.aa_mix(u, g, dU, dG, dh, 0.5, gam)
+        assert np.allclose(step, u - dU @ w + 0.5 * dh * r, rtol=0, atol=1e-10), seed
+
+
+def test_solver_aa_steps_with_dhat_and_beta():
+    """Every AA step of the oracle's solver, with the D-hat of the Remark
+    (not I), beta = 0.5 and eta = 0, on an LP whose projection is inactive
+    (free variables, '=' rows): splitting g^k = dG gamma + r with numpy's
+    least squares, the step must be u^{k+1} - u^k = -dU gamma + beta D-hat r."""
+    P = lpgen.random_lp(25, 25, nnz_per_row=5, frac_ge=0.0, frac_free=1.0, seed=7)
+    lp = O.OracleLP.from_problem(P)
+    tau, sig = _steps(P, 0.5)
+    mem, beta = 4, 0.5
+    prm = O.Params(method=1, mem=mem, tau=tau, sigma=sig, D=1e12, eta=0.0, beta=beta,
+                   dhat_mode=1)
+    K_ITERS = 10
+    r = O.solve(lp, prm, K_ITERS, trace=True, rec_len=K_ITERS + 1)
+    assert np.all(r.branch[:K_ITERS] == 1)
+    dx, dy = O.dhat(lp, 1)
+    dh = np.concatenate([dx, dy])
+    assert np.ptp(dh) > 0.1                       # D-hat is not a multiple of I here
+    U = [np.zeros(P.n + P.m)] + list(r.rec_u)     # u^0 .. u^K
+    n = P.n
+
+    def G(u):
+        xh, yh = O.T(lp, tau, sig, u[:n], u[n:])
+        return np.concatenate([xh, yh]) - u
+
+    for k in range(1, K_ITERS):
+        mk = min(mem, k)
+        dU = np.stack([U[i + 1] - U[i] for i in range(k - mk, k)], axis=1)
+        dG = np.stack([G(U[i + 1]) - G(U[i]) for i in range(k - mk, k)], axis=1)
+        g = G(U[k])
+        gam = np.linalg.lstsq(dG, g, rcond=None)[0]
+        res = g - dG @ gam
+        want = U[k] - dU @ gam + beta * dh * res
+        err = np.linalg.norm(U[k + 1] - want) / np.linalg.norm(want)
+        assert err < 1e-7, (k, err)
+
+
+# --------------------------------------------------------------------------
 # Least-squares kernels: library cross-checks and the Tikhonov bound
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("k", [1, 3, 8])

@@ -235,13 +235,13 @@ aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, do
 aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y);
 
 /* KKT residuals of a given point without any device allocation.  The paper
- * has no counterpart to this entry point; it exists for callers that cannot
- * allocate device memory when they need the residuals: code running during
- * CUDA stream capture (cudaMalloc is not capturable, cudaFree synchronises the
- * device), latency-critical loops that must avoid the implicit device
- * synchronisation of cudaMalloc / cudaFree, and programs whose device memory
- * is owned by another framework's pool.  Its scratch (block partial sums and
- * an arrival counter) is a fixed file-scope device array of
+ * has no counterpart to this entry point.  It exists for callers that cannot
+ * allocate device memory when they need the residuals: latency-critical loops
+ * that must not hit the implicit device synchronisation of cudaMalloc /
+ * cudaFree, and programs whose device memory is owned by another framework's
+ * pool or a fixed budget, where an allocation of the library's own would fail
+ * or fragment that pool.  Its scratch (block partial sums and an arrival
+ * counter) is a fixed file-scope device array of
  * AAPDHG_NOALLOC_MAX_BLOCKS * 8 doubles (1 MiB), held by every GPU that loads
  * the library until the process exits.
  *
@@ -258,15 +258,19 @@ aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y
  * enqueues work.
  * Limits and errors: returns AAPDHG_ERR_INVALID without touching the device
  * when ceil(n / 512) + ceil(m / 512) > AAPDHG_NOALLOC_MAX_BLOCKS (about 8.4M
- * rows in total), when m < 0 or n < 1, or when a required pointer is NULL;
- * AAPDHG_ERR_CUDA when the scratch address cannot be resolved or the launch
- * fails.  aapdhg_last_error does not report this entry point.
+ * rows in total), when m < 0 or n < 1, or when a required pointer is NULL
+ * (row_ptr, t_row_ptr, c, lb, ub, x and out6 always; col_idx, val, t_col_idx,
+ * t_val, row_sense, q and y when m > 0); AAPDHG_ERR_CUDA when the scratch
+ * address cannot be resolved or the launch fails.  aapdhg_last_error does not
+ * report this entry point.
  * Set-up: the first call on each device resolves the scratch array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Calls share the one scratch array: two
- * calls whose work overlaps on the same GPU (different streams, or graphs
- * launched concurrently) race and give wrong results; each call clears the
- * counter it needs before its kernel starts.                                  */
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * later calls; make that first call before any stream capture.  The kept
+ * address belongs to the device's primary context, so calling this entry
+ * point after a cudaDeviceReset of that device is not supported.  Calls
+ * share the one scratch array: two calls whose work overlaps on the same GPU
+ * (different streams, or graphs launched concurrently) race and give wrong
+ * results; each call clears the counter it needs before its kernel starts.  */
 enum { AAPDHG_NOALLOC_MAX_BLOCKS = 16384 };
 aapdhg_status aapdhg_kkt_noalloc(int32_t m, int32_t n, const int64_t *row_ptr,
                                  const int32_t *col_idx, const double *val,

@@ -1,9 +1,10 @@
 // Host runtime and C ABI of the GB300 AA-PDHG / FAA-PDHG solver.
 //
 // create():  validate the CSR of K = [G; A] (eq. LP-O), renumber rows of K and
-//            of K' longest-first, build both row-sliced CSR copies, the
-//            lanes-per-row segment tables and the split-row chunk tables, move
-//            everything to the device and form D-hat and ||q||, ||c|| there.
+//            of K' longest-first, build both matrices in two parts (rows
+//            longer than 32 entries as CSR chunks of 1024 entries, the others
+//            as SELL-32 slices), move everything to the device and form D-hat
+//            and ||q||, ||c|| there.
 // iterate(): launch the per-iteration kernel sequence in chunks on the
 //            handle's stream; poll the device-side done / error flags once per
 //            chunk.  All branch decisions (termination, safeguard, factorisation

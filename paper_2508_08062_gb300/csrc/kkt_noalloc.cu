@@ -2,13 +2,12 @@
 // caller-owned device memory, with no device allocation at all.
 //
 // Some callers cannot allocate device memory at the moment they need the
-// residuals: code that runs while a stream is being captured into a CUDA
-// graph (cudaMalloc is not capturable and cudaFree synchronises the device),
-// latency-critical loops that must not hit the implicit device
-// synchronisation of cudaMalloc/cudaFree, and hosts whose device memory is
-// entirely owned by another framework's pool.  This entry point serves them:
-// its only scratch (block partial sums and an arrival counter) is a
-// file-scope __device__ array of fixed size that every GPU loading the
+// residuals: latency-critical loops that must not hit the implicit device
+// synchronisation of cudaMalloc / cudaFree, and programs whose device memory
+// is entirely owned by another framework's pool or fixed budget, where a
+// private allocation would fail or fragment that pool.  This entry point
+// serves them: its only scratch (block partial sums and an arrival counter)
+// is a file-scope __device__ array of fixed size that every GPU loading the
 // library holds until the process exits.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -33,6 +32,8 @@ void *g_scratch_ptr[NA_MAX_DEVICES] = {nullptr};
 
 // Device address of the scratch array for the current device, resolved once
 // per device (the name is only a host-side stand-in for the device symbol).
+// The cached address belongs to the device's primary context: after a
+// cudaDeviceReset it may be stale, which the header states.
 cudaError_t scratch_for_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -159,8 +160,9 @@ extern "C" aapdhg_status aapdhg_kkt_noalloc(int32_t m, int32_t n, const int64_t 
     const int64_t bx = ((int64_t)n + NA_ROWS - 1) / NA_ROWS;
     const int64_t by = ((int64_t)m + NA_ROWS - 1) / NA_ROWS;
     if (bx + by > AAPDHG_NOALLOC_MAX_BLOCKS) return AAPDHG_ERR_INVALID;   // beyond the fixed scratch
+    // K has entries only when m > 0 (with m = 0 every row of K' is empty too)
     if (!row_ptr || !t_row_ptr || !c || !lb || !ub || !x || !out6 ||
-        (m > 0 && (!row_sense || !q || !y)))
+        (m > 0 && (!col_idx || !val || !t_col_idx || !t_val || !row_sense || !q || !y)))
         return AAPDHG_ERR_INVALID;
     double *scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) {

@@ -107,3 +107,22 @@ def test_batch_reports_the_lowest_failing_problem():
                               *[a.ctypes.data for a in arrs], binding.MIXED, None, C.byref(h))
     assert s == binding.ERR_INVALID
     assert L.aapdhg_batch_last_error(None).decode() == "problem 2: column index out of range"
+
+
+def test_kkt_noalloc_refuses_null_pointers():
+    """aapdhg_kkt_noalloc checks its pointers before any CUDA call: a NULL for
+    any array it reads gives AAPDHG_ERR_INVALID.  Its 14 array arguments come
+    first (the 15th, the stream, may be NULL); with m > 0 every array is
+    required.  Each call below has exactly one NULL array, so none of them
+    reaches the device."""
+    L = binding.load()
+    dummy = C.c_void_p(16)                    # never dereferenced: the check comes first
+    for i in range(14):
+        args = [dummy] * 14 + [None]
+        args[i] = None
+        assert L.aapdhg_kkt_noalloc(10, 20, *args) == binding.ERR_INVALID, i
+    # with m = 0 only K's row pointers, K' row pointers, c, lb, ub, x and out6 are read
+    for i in (0, 3, 8, 9, 10, 11, 13):
+        args = [dummy] * 14 + [None]
+        args[i] = None
+        assert L.aapdhg_kkt_noalloc(0, 20, *args) == binding.ERR_INVALID, i

@@ -204,6 +204,51 @@ def kernel_bytes(P, s_v, kind, M, iters, accepted, use_sum, prev_acc):
 
 
 # ---------------------------------------------------------------------------
+def time_to_tolerance(args, P_large, rank, stream, barrier):
+    """Wall-clock seconds to KKT <= 1e-4 (KKT tested every 64 iterations; the
+    time starts at the first iterate call, after the autotuner) for AA-PDHG and
+    plain PDHG on the same GPU in the same precision:
+      tiny   200 x 500, FP64, AA m = 5, no scaling (the plain-method workload);
+      medium 100k x 300k, mixed, AA m = 10, Ruiz x10 + Pock-Chambolle and the
+             primal weight update every 3000 iterations (Sec. 5.2 set-up);
+      large  2M x 5M, mixed, AA m = 20, the same set-up, capped at
+             --ttt-large-iters iterations (the unscaled LP stays far from 1e-4).
+    Each entry gives the iterations, the AA steps, the final KKT, and seconds
+    (null when the cap came first)."""
+    from paper_2508_08062_gb300 import Solver
+    cases = [("tiny_fp64", make_problem("tiny", rank), "fp64", False, 0, 5, 200000),
+             ("medium_preconditioned_U_P3000", make_problem("medium", rank), "mixed", True, 3000,
+              10, 200000)]
+    if args.workload in ("large", "banded"):
+        cases.append((f"{args.workload}_preconditioned_U_P3000", P_large, "mixed", True, 3000, 20,
+                      args.ttt_large_iters))
+    out = {}
+    for name, Q, prec, scale, period, mem, cap in cases:
+        res = {"m": Q.m, "n": Q.n, "nnz": Q.nnz, "precision": prec, "memory": mem,
+               "preconditioning": "Ruiz x10 + Pock-Chambolle" if scale else "none",
+               "primal_weight_period": period, "iteration_cap": cap}
+        with Solver(Q, precision=prec, stream=stream) as s:
+            if scale:
+                s.set_scaling(10, True)
+            nrm = s.estimate_norm(100, seed=1)
+            s.set_steps(0.9 / nrm, 0.9 / nrm)
+            s.autotune()
+            for meth in ("aa", "pdhg"):
+                s.set_method(meth, mem=mem if meth == "aa" else 0, D=10.0, eps=1.0)
+                if period:
+                    s.set_primal_weight(period=period)
+                barrier()
+                t0 = time.perf_counter()
+                conv, its = s.iterate(cap, tol=1e-4, kkt_every=64)
+                barrier()
+                dt = time.perf_counter() - t0
+                cc = s.counters()
+                res[meth] = {"converged": conv, "seconds": dt if conv else None, "iterations": its,
+                             "seconds_run": dt, "aa_steps": cc["aa_steps"], "kkt": s.get_kkt()["kkt"]}
+        out[name] = res
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -306,20 +351,6 @@ def run_ours(args):
     pd_ms = ev0.elapsed_time(ev1)
     kk = s.get_kkt()
 
-    # time to KKT <= 1e-4 (optional: the unscaled large LP does not get there in minutes)
-    ttt = None
-    if args.ttt:
-        ttt = {}
-        for meth in (wl["method"], "pdhg"):
-            s.set_method(meth, mem=M if meth != "pdhg" else 0, D=10.0, eps=1.0)
-            barrier()
-            t0 = time.perf_counter()
-            conv, its = s.iterate(args.ttt_max_iters, tol=1e-4, kkt_every=64)
-            barrier()
-            dt = time.perf_counter() - t0
-            cc = s.counters()
-            ttt[meth] = {"converged": conv, "seconds": dt if conv else None, "iterations": its,
-                         "seconds_run": dt, "aa_steps": cc["aa_steps"], "kkt": s.get_kkt()["kkt"]}
     # the AA branch every iteration (safeguard always passing): times the m x m
     # solve and the mix, which the paper's D = 10 rarely reaches on this LP
     # (a short pass from a fresh start: without the safeguard the run may
@@ -368,7 +399,6 @@ def run_ours(args):
                     "note": "safeguard D = 1e30: the AA step is attempted every iteration; "
                             "two passes of 5 + %d iterations from u^0" % n_ae}
 
-    s.close()
     libspmv = library_spmv(P) if args.library_spmv else None
 
     # end to end through the public API from pinned host buffers
@@ -401,7 +431,22 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(P, wl, tau, sig, args.workload, precondition=args.precondition)
+        cpu, ox, oy = cpu_baseline(P, wl, tau, sig, args.workload, precondition=args.precondition)
+        if wl["precision"] == "mixed":
+            # the same iterations on the GPU from u^0: how far the mixed-precision
+            # iterate is from the FP64 oracle's
+            s.set_method(wl["method"], mem=M, D=10.0, eps=1.0)
+            s.iterate(cpu["iterations"], tol=0.0, kkt_every=kkt_every)
+            gx, gy = s.get_iterate()
+            u, r = np.concatenate([gx, gy]), np.concatenate([ox, oy])
+            cpu["mixed_error_vs_oracle"] = {
+                "iterations": cpu["iterations"],
+                "rel_err": float(np.linalg.norm(u - r) / np.linalg.norm(r)),
+                "note": "||u_gpu^k - u_oracle^k|| / ||u_oracle^k|| at k = iterations, from u^0"}
+    s.close()
+
+    # time to KKT <= 1e-4 (tested every 64 iterations) for AA-PDHG and plain PDHG
+    ttt = None if (args.no_ttt or args.scale != 1.0) else time_to_tolerance(args, P, rank, stream, barrier)
 
     if rank == 0:
         line = {
@@ -532,11 +577,15 @@ def cpu_baseline(P, wl, tau, sig, workload, budget_s=20.0, precondition=False):
     t1 = time.perf_counter() - t0
     S = int(max(2, min(1000, budget_s / max(t1, 1e-6))))
     t0 = time.perf_counter()
-    O.solve(lp, prm, S)
+    r = O.solve(lp, prm, S)
     ts = time.perf_counter() - t0
-    return {"value": S / ts, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{S} FP64 oracle iterations ({wl['method']}, m={wl['mem']}) on the same "
-                      f"{workload} LP from its start (includes the initial T), 1 thread"}
+    x, y = r.x, r.y
+    if precondition:             # x = Dc x~, y = Dr y~
+        dr, dc = O.scaling(O.OracleLP.from_problem(P), 10, True)
+        x, y = dc * x, dr * y
+    return ({"value": S / ts, "unit": UNIT, "cores": 1, "kind": "oracle", "iterations": S,
+             "sample": f"{S} FP64 oracle iterations ({wl['method']}, m={wl['mem']}) on the same "
+                       f"{workload} LP from its start (includes the initial T), 1 thread"}, x, y)
 
 
 def run_batch(args):
@@ -971,7 +1020,7 @@ def run_reference(args):
         if min(P.m, P.n) > 2 else np.linalg.norm(K.toarray(), 2)
     tau = sig = 0.9 / nrm
     budget = float(os.environ.get("REF_BUDGET_S", "120"))
-    cb = cpu_baseline(P, wl, tau, sig, args.workload, budget_s=budget)
+    cb, _, _ = cpu_baseline(P, wl, tau, sig, args.workload, budget_s=budget)
     line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
             "n_gpus": world, "steps": int(cb["sample"].split()[0]), "warmup": 0,
             "requested_steps": args.steps, "requested_warmup": args.warmup,
@@ -993,9 +1042,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ttt", action="store_true",
-                    help="also time AA-PDHG and plain PDHG to KKT <= 1e-4 (KKT every 64 iterations)")
-    ap.add_argument("--ttt-max-iters", type=int, default=200000)
+    ap.add_argument("--no-ttt", action="store_true",
+                    help="skip the time-to-1e-4 leg (AA-PDHG and plain PDHG to KKT <= 1e-4)")
+    ap.add_argument("--ttt-large-iters", type=int, default=4096,
+                    help="iteration cap of the time-to-1e-4 leg on the large LP")
     ap.add_argument("--precondition", action="store_true",
                     help="Ruiz (10 passes) + Pock-Chambolle diagonal scaling before the step size")
     ap.add_argument("--profile-region", action="store_true",

@@ -46,7 +46,7 @@ typedef enum {
     AAPDHG_ERR_OOM = 2,         /* device allocation failed                     */
     AAPDHG_ERR_CUDA = 3,        /* a CUDA runtime call failed                   */
     AAPDHG_ERR_NUMERIC = 4,     /* NaN/Inf in the iterate or the KKT residual   */
-    AAPDHG_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up           */
+    AAPDHG_ERR_TIMEOUT = 5,     /* the run's time limit ran out (not sticky)    */
     AAPDHG_NOT_CONVERGED = 6    /* iteration cap reached with KKT > tol         */
 } aapdhg_status;
 
@@ -159,6 +159,15 @@ aapdhg_status aapdhg_reset(aapdhg_t h);
 aapdhg_status aapdhg_iterate(aapdhg_t h, int64_t max_iters, double tol, int32_t kkt_every,
                              int64_t *iters_done);
 
+/* Time limit of the run, in seconds of wall-clock time spent in
+ * aapdhg_iterate since the last reset (the numerical experiments of Sec. 5
+ * stop every run at KKT <= 1e-4 or one hour); 0 (the default) switches it off.
+ * aapdhg_iterate checks it between chunks of 64 iterations and, once it has
+ * run out, returns AAPDHG_ERR_TIMEOUT with *iters_done set.  The status is not
+ * sticky: the run stays at its last iterate and continues under a new limit.
+ * seconds must be finite and >= 0 (AAPDHG_ERR_INVALID otherwise).           */
+aapdhg_status aapdhg_set_time_limit(aapdhg_t h, double seconds);
+
 /* Current iterate u^k: x (n doubles) and y (m doubles) in the caller's row and
  * column order; either pointer may be NULL.                                   */
 aapdhg_status aapdhg_get_iterate(aapdhg_t h, double *x, double *y);
@@ -183,6 +192,20 @@ aapdhg_status aapdhg_get_counters(aapdhg_t h, int64_t *aa_steps, int64_t *pdhg_s
 aapdhg_status aapdhg_set_trace(aapdhg_t h, int64_t capacity);
 aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double *gnorm,
                                double *kkt, int32_t *mk);
+
+/* Test hook: the Anderson memory of Alg. 2 as the device holds it after the
+ * last iteration k (the columns of dG^{k-m_k} and the incremental Gram matrix
+ * of Sec. 5).  *count (optional) receives the number of columns c; gram
+ * (c x c, row-major) = <dg_a, dg_b> and rhs (c) = <dg_a, g^k>, columns oldest
+ * first, as accumulated on the device (FP64, or float-float pairs summed in
+ * FP64 in mixed mode); dg (c x (n + m), column a at a * (n + m)) and g
+ * (n + m) = g^k hold the stored vectors in the caller's variable then
+ * constraint order, in the solver's units (scaled when aapdhg_set_scaling was
+ * applied), FP32 values widened exactly in mixed mode.  Any output may be
+ * NULL; capacity below c gives AAPDHG_ERR_INVALID (with *count set).  No
+ * columns before the first iteration or for plain PDHG.                     */
+aapdhg_status aapdhg_get_memory(aapdhg_t h, int32_t capacity, int32_t *count, double *gram,
+                                double *rhs, double *dg, double *g);
 
 /* Kernel instrumentation for benchmarks.  aapdhg_profile_kernels(h, 1) makes
  * aapdhg_iterate bracket every kernel it launches with CUDA events recorded on

@@ -30,9 +30,10 @@ PRECISIONS = {"fp64": FP64, "mixed": MIXED}
 # every entry point declared in include/aapdhg.h
 EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_estimate_norm",
            "aapdhg_set_method", "aapdhg_set_scaling", "aapdhg_set_start", "aapdhg_reset",
-           "aapdhg_iterate",
+           "aapdhg_iterate", "aapdhg_set_time_limit",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
-           "aapdhg_get_trace", "aapdhg_profile_kernels", "aapdhg_get_kernel_profile",
+           "aapdhg_get_trace", "aapdhg_get_memory", "aapdhg_profile_kernels",
+           "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
            "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_batch_autotune",
            "aapdhg_set_primal_weight",
@@ -83,11 +84,13 @@ def load(path: str = LIB_PATH):
     L.aapdhg_set_start.argtypes = [vp, vp, vp]
     L.aapdhg_reset.argtypes = [vp]
     L.aapdhg_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
+    L.aapdhg_set_time_limit.argtypes = [vp, f64]
     L.aapdhg_get_iterate.argtypes = [vp, vp, vp]
     L.aapdhg_get_kkt.argtypes = [vp, vp]
     L.aapdhg_get_counters.argtypes = [vp, vp, vp, vp, vp]
     L.aapdhg_set_trace.argtypes = [vp, i64]
     L.aapdhg_get_trace.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
+    L.aapdhg_get_memory.argtypes = [vp, i32, vp, vp, vp, vp, vp]
     L.aapdhg_profile_kernels.argtypes = [vp, i32]
     L.aapdhg_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
     L.aapdhg_kkt_noalloc.argtypes = [i32, i32] + [vp] * 15
@@ -278,11 +281,21 @@ class Solver:
         self._check(self._L.aapdhg_reset(self._h))
 
     def iterate(self, max_iters, tol=0.0, kkt_every=0):
+        """Returns (converged, iterations run).  Raises AAPDHGError on an error,
+        including AAPDHG_ERR_TIMEOUT when the time limit ran out (not sticky)."""
         done = C.c_int64()
-        s = self._check(self._L.aapdhg_iterate(self._h, int(max_iters), float(tol),
-                                               int(kkt_every), C.byref(done)),
-                        allow=(OK, NOT_CONVERGED))
+        s = self._L.aapdhg_iterate(self._h, int(max_iters), float(tol), int(kkt_every),
+                                   C.byref(done))
+        if s == ERR_TIMEOUT:
+            err = AAPDHGError(s, "time limit ran out")
+            err.iters_done = done.value
+            raise err
+        self._check(s, allow=(OK, NOT_CONVERGED))
         return s == OK, done.value
+
+    def set_time_limit(self, seconds):
+        """Wall-clock limit of the run in seconds (0: none)."""
+        self._check(self._L.aapdhg_set_time_limit(self._h, float(seconds)))
 
     def get_iterate(self):
         x = np.empty(self.n)
@@ -330,6 +343,18 @@ class Solver:
     def set_task_shape(self, shape_x, shape_y):
         """Fix the half-step task shapes ((-1, -1): tune again at the next iterate)."""
         self._check(self._L.aapdhg_set_task_shape(self._h, int(shape_x), int(shape_y)))
+
+    def get_memory(self, capacity=32):
+        """The Anderson memory after the last iteration (test hook): Gram matrix and
+        right-hand side (oldest column first), the dG columns (count, n + m) and g^k."""
+        cnt = C.c_int32()
+        N = self.n + self.m
+        gram = np.zeros(capacity * capacity); rhs = np.zeros(capacity)
+        dg = np.zeros((capacity, N)); g = np.zeros(N)
+        self._check(self._L.aapdhg_get_memory(self._h, int(capacity), C.byref(cnt), _ptr(gram),
+                                               _ptr(rhs), _ptr(dg), _ptr(g)))
+        k = cnt.value
+        return dict(count=k, gram=gram[:k * k].reshape(k, k), rhs=rhs[:k], dg=dg[:k], g=g)
 
     KERNEL_KINDS = ("xstep", "ystep", "memory", "mix")
 

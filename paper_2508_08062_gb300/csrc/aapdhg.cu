@@ -10,6 +10,7 @@
 //            chunk.  All branch decisions (termination, safeguard, factorisation
 //            failure, filters) are taken on the device.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -359,6 +360,8 @@ struct aapdhg_s {
     // task shapes of the two half-step kernels (autotuned at the first iterate)
     int32_t shape_x = 0, shape_y = 0;
     bool tuned = false, autotune = true;
+    // time limit of a run (the paper's one-hour cap); 0: none
+    double time_limit = 0.0, time_used = 0.0;
     int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
     double tune_us[2 * NSHAPE] = {};
     // primal weight update (off when pw_period = 0)
@@ -610,6 +613,7 @@ template <typename V> aapdhg_status ensure_rings(aapdhg_t h, int32_t M) {
 void drop_graphs(aapdhg_t h);
 
 template <typename V> aapdhg_status reset_run(aapdhg_t h) {
+    h->time_used = 0.0;
     typedef typename Vec2<V>::T V2;
     Prob<V> &P = prob<V>(h);
     const int32_t n = h->n, m = h->m;
@@ -919,7 +923,18 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
     const int64_t it0 = h->st_host->it;
     int64_t hit = it0, launched = 0;
     bool done = false;
+    const auto t_start = std::chrono::steady_clock::now();
     while (launched < max_iters && !done) {
+        if (h->time_limit > 0.0) {
+            // checked between chunks, after the last chunk's state was read
+            const double t = h->time_used +
+                std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+            if (t > h->time_limit) {
+                h->time_used = t;
+                if (done_iters) *done_iters = hit - it0;
+                return AAPDHG_ERR_TIMEOUT;
+            }
+        }
         int64_t chunk = std::min<int64_t>(CHUNK_ITERS, max_iters - launched);
         if (h->pw_period > 0) {
             // the current iterate is u^k with k = hit + 1; updates at k = 0 mod U_P,
@@ -946,6 +961,7 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
         hit = h->st_host->it;
     }
     (void)P;
+    h->time_used += std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
     if (done_iters) *done_iters = hit - it0;
     if (done) return AAPDHG_OK;
     // max_iters may also end exactly on a converged iterate that was not tested
@@ -971,6 +987,45 @@ template <typename V> aapdhg_status get_iterate_t(aapdhg_t h, double *x, double 
             const double v = (double)(cur ? up[h->n + i].y : up[h->n + i].x);
             y[h->perm_y[i]] = h->scaled ? v * h->dr_host[i] : v;      // y = Dr y~
         }
+    return AAPDHG_OK;
+}
+
+// The Anderson memory as the device holds it after the last iteration: the
+// Gram matrix and right-hand side in list order, the dG columns and g^k in
+// the caller's element order (FP32 values widened exactly in mixed mode).
+template <typename V> aapdhg_status get_memory_t(aapdhg_t h, int32_t capacity, int32_t *count,
+                                                 double *gram, double *rhs, double *dg, double *g) {
+    Prob<V> &P = prob<V>(h);
+    aapdhg_status s = read_state(h);
+    if (s != AAPDHG_OK) return s;
+    const DevState &st = *h->st_host;
+    const int k = (h->mp.method == 0 || h->mp.mem == 0 || !P.DG || !st.init_done) ? 0 : st.count;
+    if (count) *count = k;
+    if (k > capacity) return fail(h, AAPDHG_ERR_INVALID, "get_memory: capacity below the column count");
+    const int32_t n = h->n, m = h->m;
+    const int64_t N = h->N;
+    for (int a = 0; a < k; ++a) {
+        if (rhs) rhs[a] = st.rhs[st.list[a]];
+        if (gram)
+            for (int b = 0; b < k; ++b) gram[a * k + b] = st.G[st.list[a] * NSLOT + st.list[b]];
+    }
+    std::vector<V> col(N);
+    auto to_caller = [&](double *out) {
+        for (int32_t j = 0; j < n; ++j) out[h->perm_x[j]] = (double)col[j];
+        for (int32_t i = 0; i < m; ++i) out[n + h->perm_y[i]] = (double)col[n + i];
+    };
+    if (dg)
+        for (int a = 0; a < k; ++a) {
+            CK(h, cudaMemcpyAsync(col.data(), P.DG + (int64_t)st.list[a] * P.Npad, sizeof(V) * N,
+                                  cudaMemcpyDeviceToHost, h->stream));
+            CK(h, cudaStreamSynchronize(h->stream));
+            to_caller(dg + (int64_t)a * N);
+        }
+    if (g) {
+        CK(h, cudaMemcpyAsync(col.data(), P.g, sizeof(V) * N, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaStreamSynchronize(h->stream));
+        to_caller(g);
+    }
     return AAPDHG_OK;
 }
 
@@ -1284,6 +1339,23 @@ aapdhg_status aapdhg_get_iterate(aapdhg_t h, double *x, double *y) {
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     return h->prec == AAPDHG_FP64 ? get_iterate_t<double>(h, x, y) : get_iterate_t<float>(h, x, y);
+}
+
+aapdhg_status aapdhg_set_time_limit(aapdhg_t h, double seconds) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!(seconds >= 0.0) || std::isinf(seconds))
+        return fail(h, AAPDHG_ERR_INVALID, "time limit must be finite and >= 0");
+    h->time_limit = seconds;
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_get_memory(aapdhg_t h, int32_t capacity, int32_t *count, double *gram,
+                                double *rhs, double *dg, double *g) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    return h->prec == AAPDHG_FP64 ? get_memory_t<double>(h, capacity, count, gram, rhs, dg, g)
+                                  : get_memory_t<float>(h, capacity, count, gram, rhs, dg, g);
 }
 
 aapdhg_status aapdhg_get_kkt(aapdhg_t h, double *out6) {

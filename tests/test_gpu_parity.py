@@ -197,8 +197,9 @@ def test_mixed_precision_final_objective(method):
     assert o["kkt"] <= 1.05e-4, o
     assert abs(g["kkt"] - o["kkt"]) <= 1e-3 * o["kkt"] + 1e-9
     pref = float(P.c @ ref.x)
-    # both points are 1e-4-optimal; their objectives agree to that order
-    assert abs(o["pobj"] - pref) <= 2e-4 * (1 + abs(pref)), (o["pobj"], pref)
+    # both points are 1e-4-optimal and stop at different checks; measured
+    # objective differences are ~1e-6 (tests/test_gpu_mixed_precision.py states them)
+    assert abs(o["pobj"] - pref) <= 2e-5 * (1 + abs(pref)), (o["pobj"], pref)
     print(method, "gpu iters", its, "oracle iters", ref.iters, "rel obj diff",
           abs(o["pobj"] - pref) / (1 + abs(pref)))
 

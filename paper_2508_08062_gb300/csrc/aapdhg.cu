@@ -468,6 +468,14 @@ int grid_for(aapdhg_t h, int64_t blocks_needed, int occ) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(blocks_needed, cap));
 }
 
+// D-hat (mode 1: the Remark on its construction; 0: identity) of the current K.
+template <typename V> void launch_dhat(aapdhg_t h, int mode, cudaStream_t s) {
+    Prob<V> &P = prob<V>(h);
+    const int64_t tasks = (int64_t)P.KT.n_long + P.KT.n_slices + P.K.n_long + P.K.n_slices;
+    k_dhat_sliced<V><<<grid_for(h, (std::max(tasks, h->N / 32) + WARPS - 1) / WARPS, 8), BLOCK, 0, s>>>(
+        P.KT, P.K, h->n, mode, const_cast<V *>(P.dh));
+}
+
 // Kernel kinds of the instrumentation.
 enum { KIND_XSTEP = 0, KIND_YSTEP = 1, KIND_MEMORY = 2, KIND_MIX = 3 };
 
@@ -585,8 +593,7 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
 
     // D-hat and the norms ||q||, ||c|| on the device
     const int gE = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
-    k_dhat<V><<<grid_for(h, (N + WARPS - 1) / WARPS, 8), BLOCK, 0, h->stream>>>(P.KT, P.K, n, m, 1,
-                                                                             const_cast<V *>(P.dh));
+    launch_dhat<V>(h, 1, h->stream);
     h->dhat_mode = 1;
     k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.q, m, P.part3, h->st, 0);
     k_norm2<V><<<gE, BLOCK, 0, h->stream>>>(P.c, n, P.part3, h->st, 1);
@@ -1125,9 +1132,7 @@ template <typename V> aapdhg_status set_scaling_t(aapdhg_t h, int32_t ruiz_iters
     P.sc_x = scx;
     P.sc_y = m > 0 ? scy : nullptr;
     // D-hat of the scaled K
-    const int gD = grid_for(h, (h->N + WARPS - 1) / WARPS, 8);
-    k_dhat<V><<<gD, BLOCK, 0, s>>>(P.KT, P.K, n, m, h->dhat_mode < 0 ? 1 : h->dhat_mode,
-                                   const_cast<V *>(P.dh));
+    launch_dhat<V>(h, h->dhat_mode < 0 ? 1 : h->dhat_mode, s);
     CK(h, cudaGetLastError());
     h->pw_base_valid = false;
     h->scaled = true;
@@ -1274,13 +1279,8 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
     drop_graphs(h);
     // D-hat recomputed on the device when the requested mode differs
     if (dhat_mode != h->dhat_mode) {
-        const int gD = grid_for(h, (h->N + WARPS - 1) / WARPS, 8);
-        if (h->prec == AAPDHG_FP64)
-            k_dhat<double><<<gD, BLOCK, 0, h->stream>>>(h->pd.KT, h->pd.K, h->n, h->m, dhat_mode,
-                                                        const_cast<double *>(h->pd.dh));
-        else
-            k_dhat<float><<<gD, BLOCK, 0, h->stream>>>(h->pf.KT, h->pf.K, h->n, h->m, dhat_mode,
-                                                       const_cast<float *>(h->pf.dh));
+        if (h->prec == AAPDHG_FP64) launch_dhat<double>(h, dhat_mode, h->stream);
+        else launch_dhat<float>(h, dhat_mode, h->stream);
         CK(h, cudaGetLastError());
         h->dhat_mode = dhat_mode;
         h->pw_base_valid = false;

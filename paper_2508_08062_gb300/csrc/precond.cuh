@@ -86,6 +86,49 @@ __global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mo
     }
 }
 
+// The same D-hat for one LP in the half-steps' layout (rows longest first:
+// rows 0 .. n_long - 1 are long CSR rows, slice q holds rows n_long + 32 q
+// on), one warp task per long row or per SELL slice: a long row is reduced by
+// its warp, a slice by one lane per row with coalesced loads.  |entry| and
+// max are exact in any precision and order, so the result equals k_dhat's.
+template <typename V>
+__device__ __forceinline__ void dhat_task(const CSRView<V> &A, int64_t t, V *out) {
+    const int lane = threadIdx.x & 31;
+    V mx = V(0);
+    int64_t r;
+    if (t < A.n_long) {
+        r = t;
+        for (int32_t k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) mx = fmax(mx, fabs(A.val[k]));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane != 0) return;
+    } else {
+        const int64_t q = t - A.n_long;
+        r = A.n_long + q * 32 + lane;
+        if (r >= A.rows) return;
+        const int4 meta = A.slice_meta[q];      // offset, width (padding entries are 0)
+        for (int tt = 0; tt < meta.y; ++tt) mx = fmax(mx, fabs(A.sell_val[(int64_t)meta.x + (int64_t)tt * 32 + lane]));
+    }
+    out[r] = (V)sqrt(fmax((double)mx, 1e-10));
+}
+
+template <typename V>
+__global__ void k_dhat_sliced(CSRView<V> KT, CSRView<V> K, int32_t n, int mode, V *dh) {
+    const int64_t tx = (int64_t)KT.n_long + KT.n_slices, ty = (int64_t)K.n_long + K.n_slices;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t w0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (mode == 0) {
+        for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n + K.rows;
+             e += (int64_t)gridDim.x * blockDim.x)
+            dh[e] = V(1);
+        return;
+    }
+    for (int64_t t = w0; t < tx + ty; t += warps) {
+        if (t < tx) dhat_task(KT, t, dh);
+        else dhat_task(K, t - tx, dh + n);
+    }
+}
+
 // Primal weight update (Alg. "Primal weight update"): ||x^k - x^{k-U_P}||^2
 // and ||y^k - y^{k-U_P}||^2 against the snapshot (into st->scratch[2], [3] by
 // the last block), and the snapshot <- u^k.  copy_only: the snapshot alone.

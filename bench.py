@@ -196,8 +196,9 @@ def kernel_bytes(P, s_v, kind, M, iters, accepted, use_sum, prev_acc):
     if kind == "ystep":
         return iters * (Z * (s_v + 4) + 2 * s_v * n + 6 * s_v * m)
     if kind == "memory":
-        nold = max(M - 1, 0)
-        return (iters * N * s_v * (7 + nold) + prev_acc * N * s_v) if M > 0 else 0
+        return (iters * N * s_v * 7 + prev_acc * N * s_v) if M > 0 else 0
+    if kind == "gram":          # an AA attempt reads the M memory columns and g^k
+        return accepted * N * s_v * (M + 1) if M > 0 else 0
     if kind == "mix":
         return accepted * N * s_v * 8 + use_sum * N * s_v
     return 0
@@ -529,6 +530,7 @@ def library_spmv(P, reps=20):
 
 KERNEL_FILES = {"xstep": ("common.cuh", "spmv.cuh"), "ystep": ("common.cuh", "spmv.cuh"),
                 "memory": ("common.cuh", "anderson.cuh"), "mix": ("common.cuh", "anderson.cuh"),
+                "gram": ("common.cuh", "anderson.cuh"),
                 "batch:xstep": ("common.cuh", "spmv.cuh", "batch.cuh"),
                 "batch:ystep": ("common.cuh", "spmv.cuh", "batch.cuh"),
                 "batch:memory": ("common.cuh", "anderson.cuh", "batch.cuh")}

@@ -198,7 +198,12 @@ aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double 
  * of Sec. 5).  *count (optional) receives the number of columns c; gram
  * (c x c, row-major) = <dg_a, dg_b> and rhs (c) = <dg_a, g^k>, columns oldest
  * first, as accumulated on the device (FP64, or float-float pairs summed in
- * FP64 in mixed mode); dg (c x (n + m), column a at a * (n + m)) and g
+ * FP64 in mixed mode).  The device forms a new column's entries with the
+ * other columns, and the right-hand side, at the next AA attempt (an
+ * iteration whose safeguard test passed): after an iteration without one,
+ * the entries of the columns added since the last attempt, and rhs except
+ * for the newest column, are pending (left as they were).  dg (c x (n + m),
+ * column a at a * (n + m)) and g
  * (n + m) = g^k hold the stored vectors in the caller's variable then
  * constraint order, in the solver's units (scaled when aapdhg_set_scaling was
  * applied), FP32 values widened exactly in mixed mode.  Any output may be
@@ -211,8 +216,10 @@ aapdhg_status aapdhg_get_memory(aapdhg_t h, int32_t capacity, int32_t *count, do
  * aapdhg_iterate bracket every kernel it launches with CUDA events recorded on
  * the handle's stream and accumulate the elapsed times per kernel kind; it
  * resets the totals (0 turns the events off).  aapdhg_get_kernel_profile
- * returns, for kind 0 (x-step over K'), 1 (y-step over K), 2 (memory pass and
- * m x m solve) or 3 (AA mix), the launches and total milliseconds since the
+ * returns, for kind 0 (x-step over K'), 1 (y-step over K), 2 (memory pass:
+ * the new column, and the m x m work of an iteration without an AA attempt),
+ * 3 (AA mix) or 4 (Gram pass and m x m solve of an AA attempt), the launches
+ * and total milliseconds since the
  * last reset; kind -1 returns the number of kernels aapdhg_iterate launched
  * since create (counted with or without events) and 0 ms.                    */
 aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable);

@@ -356,7 +356,7 @@ class Solver:
         k = cnt.value
         return dict(count=k, gram=gram[:k * k].reshape(k, k), rhs=rhs[:k], dg=dg[:k], g=g)
 
-    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix")
+    KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "gram")
 
     def profile_kernels(self, enable=True):
         """CUDA-event timing of every kernel launched by iterate (resets totals)."""

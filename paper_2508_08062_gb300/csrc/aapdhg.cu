@@ -343,8 +343,8 @@ struct aapdhg_s {
     bool prof_on = false;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_kind;
-    double prof_ms[4] = {0, 0, 0, 0};
-    int64_t prof_n[4] = {0, 0, 0, 0};
+    double prof_ms[5] = {0, 0, 0, 0, 0};
+    int64_t prof_n[5] = {0, 0, 0, 0, 0};
     int64_t launches = 0;
     // CUDA graphs of full chunks, keyed by the KKT phase of the chunk's first
     // iteration; invalidated whenever kernel parameters change
@@ -354,6 +354,7 @@ struct aapdhg_s {
         int64_t phase;
         int32_t kkt_every;
         double tol;
+        int64_t kernels;               // kernel launches in the captured chunk
     };
     std::vector<GraphEntry> graphs;
     bool use_graphs = true;
@@ -477,7 +478,7 @@ template <typename V> void launch_dhat(aapdhg_t h, int mode, cudaStream_t s) {
 }
 
 // Kernel kinds of the instrumentation.
-enum { KIND_XSTEP = 0, KIND_YSTEP = 1, KIND_MEMORY = 2, KIND_MIX = 3 };
+enum { KIND_XSTEP = 0, KIND_YSTEP = 1, KIND_MEMORY = 2, KIND_MIX = 3, KIND_GRAM = 4, NKIND = 5 };
 
 void mark_begin(aapdhg_t h, int kind) {
     h->launches += 1;
@@ -575,16 +576,17 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     }
     P.grid1 = h->gridx[0];
     P.grid2 = h->gridy[0];
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V, 20>, BLOCK, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V>, BLOCK, 0);
 
     P.grid3 = grid_for(h, (N + BLOCK - 1) / BLOCK, std::max(occ3, 1));
     h->grid5 = grid_for(h, (N + BLOCK - 1) / BLOCK, 4);
     P.part1 = (double *)dev_alloc(h, sizeof(double) * 4 * gmax1);
     P.part2 = (double *)dev_alloc(h, sizeof(double) * 3 * gmax2);
     P.part3 = (double *)dev_alloc(h, sizeof(double) * (MAXM + 3) * h->sm_count * 8);
+    P.part4 = (double *)dev_alloc(h, sizeof(double) * GRAM_MAXPAIRS * h->sm_count * GRAM_MAX_OCC);
     h->st = (DevState *)dev_alloc(h, sizeof(DevState));
     P.st = h->st;
-    if (!P.part1 || !P.part2 || !P.part3 || !h->st) ok = false;
+    if (!P.part1 || !P.part2 || !P.part3 || !P.part4 || !h->st) ok = false;
     if (!ok) return fail(h, AAPDHG_ERR_OOM, "device allocation or copy failed during create");
     CK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
     P.DG = P.W = nullptr;
@@ -670,29 +672,45 @@ template <typename V> aapdhg_status reset_run(aapdhg_t h) {
     return AAPDHG_OK;
 }
 
+// The device stopped the run: st->error 1 = NaN/Inf met, 2 = a bounded wait
+// of the Gram pass on its bulk copies gave up.
+aapdhg_status device_error(aapdhg_t h) {
+    if (h->st_host->error == 2)
+        return fail(h, AAPDHG_ERR_CUDA, "a bounded device-side wait (Gram pass copies) gave up");
+    return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
+}
+
 aapdhg_status reset_any(aapdhg_t h) {
     return h->prec == AAPDHG_FP64 ? reset_run<double>(h) : reset_run<float>(h);
 }
 
-template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode) {
+template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode, int fin) {
     Prob<V> &P = prob<V>(h);
     const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
-    // grid of the memory pass for this instance: all resident blocks (fixed per
-    // instance, so its block partials are summed in a fixed order)
-    static int occ_mem = 0, occ_mix = 0;
+    // grids of the memory and Gram passes for this instance: all resident
+    // blocks (fixed per instance, so their block partials are summed in a
+    // fixed order)
+    static int occ_mem = 0, occ_mix = 0, occ_gram = 0;
     if (occ_mem == 0) {
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_mem, k_memory<V, MC>, BLOCK, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_mem, k_memory<V>, BLOCK, 0);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_mix, k_mix<V, MC>, BLOCK, 0);
+        cudaFuncSetAttribute(k_gram<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, gram_dyn_smem(MAXM));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_gram, k_gram<V>, BLOCK, gram_dyn_smem(MC));
         occ_mem = std::max(occ_mem, 1);
         occ_mix = std::max(occ_mix, 1);
+        occ_gram = std::min(std::max(occ_gram, 1), GRAM_MAX_OCC);
     }
     P.grid3 = M > 0 ? grid_for(h, (h->N + BLOCK * 4 - 1) / (BLOCK * 4), occ_mem) : 1;
+    P.grid4 = M > 0 ? grid_for(h, (h->N + 127) / 128, occ_gram) : 1;
     const int g5 = grid_for(h, (h->N + BLOCK * 4 - 1) / (BLOCK * 4), occ_mix);
     const int g3 = P.grid3;
     mark_begin(h, KIND_MEMORY);
-    k_memory<V, MC><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode);
+    k_memory<V><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode, fin);
     mark_end(h);
     if (mode == MODE_ITER && M > 0) {
+        mark_begin(h, KIND_GRAM);
+        k_gram<V><<<P.grid4, BLOCK, gram_dyn_smem(M), h->stream>>>(P, h->mp);
+        mark_end(h);
         mark_begin(h, KIND_MIX);
         k_mix<V, MC><<<g5, BLOCK, 0, h->stream>>>(P, h->mp);
         mark_end(h);
@@ -717,7 +735,7 @@ template <typename V, bool KKT> void launch_y(aapdhg_t h, int shape, int mode) {
     else k_ystep<V, KKT, 0><<<P.grid2, BLOCK, 0, h->stream>>>(P, h->mp, mode);
 }
 
-template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
+template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode, bool with_finalize = true) {
     mark_begin(h, KIND_XSTEP);
     if (kkt) launch_x<V, true>(h, h->shape_x, mode);
     else launch_x<V, false>(h, h->shape_x, mode);
@@ -725,8 +743,10 @@ template <typename V> void launch_T(aapdhg_t h, bool kkt, int mode) {
     mark_begin(h, KIND_YSTEP);                 // the y-step and its final reduction
     if (kkt) launch_y<V, true>(h, h->shape_y, mode);
     else launch_y<V, false>(h, h->shape_y, mode);
-    k_finalize<V><<<1, BLOCK, 0, h->stream>>>(prob<V>(h), h->mp, mode, kkt ? 1 : 0);
-    h->launches += 1;
+    if (with_finalize) {
+        k_finalize<V><<<1, BLOCK, 0, h->stream>>>(prob<V>(h), h->mp, mode, kkt ? 1 : 0);
+        h->launches += 1;
+    }
     mark_end(h);
 }
 
@@ -788,18 +808,22 @@ template <typename V> aapdhg_status autotune_t(aapdhg_t h) {
     return AAPDHG_OK;
 }
 
-template <typename V> void launch_memory_any(aapdhg_t h, int mode) {
+template <typename V> void launch_memory_any(aapdhg_t h, int mode, int fin) {
     const int M = h->mp.mem;
-    if (M <= 4) launch_memory_mix<V, 4>(h, mode);
-    else if (M <= 8) launch_memory_mix<V, 8>(h, mode);
-    else if (M <= 16) launch_memory_mix<V, 16>(h, mode);
-    else if (M <= 20) launch_memory_mix<V, 20>(h, mode);
-    else launch_memory_mix<V, 32>(h, mode);
+    if (M <= 4) launch_memory_mix<V, 4>(h, mode, fin);
+    else if (M <= 8) launch_memory_mix<V, 8>(h, mode, fin);
+    else if (M <= 16) launch_memory_mix<V, 16>(h, mode, fin);
+    else if (M <= 20) launch_memory_mix<V, 20>(h, mode, fin);
+    else launch_memory_mix<V, 32>(h, mode, fin);
 }
 
+// One loop iteration.  Without a KKT test (the iteration cannot stop) the
+// half-steps' final reduction runs in the memory pass's last block instead
+// of a launch of its own.
 template <typename V> void launch_iteration(aapdhg_t h, bool kkt, int mode) {
-    launch_T<V>(h, kkt, mode);
-    if (mode != MODE_EVAL) launch_memory_any<V>(h, mode);
+    const bool fuse = mode == MODE_ITER && !kkt;
+    launch_T<V>(h, kkt, mode, !fuse);
+    if (mode != MODE_EVAL) launch_memory_any<V>(h, mode, fuse ? 1 : 0);
 }
 
 aapdhg_status read_state(aapdhg_t h, bool full = true) {
@@ -825,7 +849,7 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
     for (auto &g : h->graphs)
         if (g.phase == phase && g.kkt_every == kkt_every && g.tol == tol) {
             if (cudaGraphLaunch(g.exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
-            h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 5 : 4);
+            h->launches += g.kernels;
             return true;
         }
     if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -847,6 +871,7 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
         ok = cudaStreamEndCapture(h->cap_stream, &graph) == cudaSuccess;
     }
     h->stream = user;
+    const int64_t kernels = h->launches - saved;
     h->launches = saved;
     cudaGraphExec_t exec = nullptr;
     if (ok) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
@@ -856,9 +881,9 @@ template <typename V> bool launch_chunk_graph(aapdhg_t h, int64_t hit, int32_t k
         h->use_graphs = false;
         return false;
     }
-    h->graphs.push_back({exec, phase, kkt_every, tol});
+    h->graphs.push_back({exec, phase, kkt_every, tol, kernels});
     if (cudaGraphLaunch(exec, h->stream) != cudaSuccess) { cudaGetLastError(); return false; }
-    h->launches += (int64_t)CHUNK_ITERS * ((h->mp.method != 0 && h->mp.mem > 0) ? 5 : 4);
+    h->launches += kernels;
     return true;
 }
 
@@ -924,7 +949,7 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
         CK(h, cudaGetLastError());
         if ((s = read_state(h)) != AAPDHG_OK) return s;
     }
-    if (h->st_host->error) return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
+    if (h->st_host->error) return device_error(h);
     // a new call re-tests the current iterate against its own tolerance
     CK(h, cudaMemsetAsync(&h->st->done, 0, sizeof(int32_t), h->stream));
     const int64_t it0 = h->st_host->it;
@@ -963,7 +988,7 @@ template <typename V> aapdhg_status iterate_t(aapdhg_t h, int64_t max_iters, dou
         CK(h, cudaGetLastError());
         launched += chunk;
         if ((s = read_state(h, false)) != AAPDHG_OK) return s;
-        if (h->st_host->error) return fail(h, AAPDHG_ERR_NUMERIC, "NaN or Inf in the iterate");
+        if (h->st_host->error) return device_error(h);
         done = h->st_host->done != 0;
         hit = h->st_host->it;
     }
@@ -1423,13 +1448,13 @@ aapdhg_status aapdhg_profile_kernels(aapdhg_t h, int32_t enable) {
     CK(h, cudaStreamSynchronize(h->stream));
     collect_marks(h);
     h->prof_on = enable != 0;
-    for (int k = 0; k < 4; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
+    for (int k = 0; k < NKIND; ++k) { h->prof_ms[k] = 0.0; h->prof_n[k] = 0; }
     return AAPDHG_OK;
 }
 
 aapdhg_status aapdhg_get_kernel_profile(aapdhg_t h, int32_t kind, int64_t *launches,
                                         double *total_ms) {
-    if (!h || kind < -1 || kind > 3) return AAPDHG_ERR_INVALID;
+    if (!h || kind < -1 || kind >= NKIND) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     CK(h, cudaStreamSynchronize(h->stream));
     collect_marks(h);

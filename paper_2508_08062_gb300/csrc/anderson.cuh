@@ -21,6 +21,7 @@
 //              roles of the two iterate components swap and du = g^k.
 #pragma once
 #include "common.cuh"
+#include "spmv.cuh"
 
 namespace aap {
 
@@ -207,35 +208,16 @@ static __device__ bool gram_solve(DevState *st, const int *cols, int k, double e
     return ok;
 }
 
-// The m x m work of one iteration for one LP, run by warp 0 of one block after
-// the memory pass's partial sums are reduced into red[]: the Gram row and
-// column of the new slot, the incremental right-hand side, the column list,
-// and, when the safeguard passed (st->want_aa), the solve of Alg. 2 or the
-// filters and solve of Alg. 3; then the counters and the next free slot.
-template <int MC>
-__device__ void memory_finalize(DevState *st, const MethodParams &mp, int M, const int *s_old,
-                                int nold, int sn, const double *red, SolveSmem &sm, const Trace &tr) {
+// The rest of an iteration's m x m work once the Gram matrix, the right-hand
+// side and the column list are current, run by warp 0 of one block: when the
+// safeguard passed (st->want_aa), the solve of Alg. 2 or the filters and
+// solve of Alg. 3; then the slot for the next column, the counters and the
+// trace.
+static __device__ void memory_solve_tail(DevState *st, const MethodParams &mp, int M, SolveSmem &sm,
+                                  const Trace &tr) {
     const int lane = threadIdx.x & 31;
     int accept = 0, lsfail = 0;
     if (M > 0) {
-        // Gram row / column of the new slot; incremental right-hand side
-        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
-        for (int t = lane; t < nold; t += 32) {
-            const int s = s_old[t];
-            st->G[s * NSLOT + sn] = red[t];
-            st->G[sn * NSLOT + s] = red[t];
-            st->rhs[s] += red[t];
-            st->list[t] = s;
-        }
-        if (lane == 0) {
-            st->G[sn * NSLOT + sn] = red[MC];
-            st->rhs[sn] = red[MC + 1];
-            st->en2[sn] = red[MC + 2];
-            st->list[nold] = sn;
-            st->count = nold + 1;
-            st->new_slot = sn;
-        }
-        __syncwarp();
         if (st->want_aa) {
             const int k = st->count;
             if (mp.method == 1) {
@@ -280,6 +262,38 @@ __device__ void memory_finalize(DevState *st, const MethodParams &mp, int M, con
         }
         st->it = it + 1;
     }
+}
+
+// The m x m work of one iteration for one LP, run by warp 0 of one block after
+// the memory pass's partial sums are reduced into red[]: the Gram row and
+// column of the new slot, the incremental right-hand side, the column list,
+// and, when the safeguard passed (st->want_aa), the solve of Alg. 2 or the
+// filters and solve of Alg. 3; then the counters and the next free slot.
+template <int MC>
+__device__ void memory_finalize(DevState *st, const MethodParams &mp, int M, const int *s_old,
+                                int nold, int sn, const double *red, SolveSmem &sm, const Trace &tr) {
+    const int lane = threadIdx.x & 31;
+    if (M > 0) {
+        // Gram row / column of the new slot; incremental right-hand side
+        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
+        for (int t = lane; t < nold; t += 32) {
+            const int s = s_old[t];
+            st->G[s * NSLOT + sn] = red[t];
+            st->G[sn * NSLOT + s] = red[t];
+            st->rhs[s] += red[t];
+            st->list[t] = s;
+        }
+        if (lane == 0) {
+            st->G[sn * NSLOT + sn] = red[MC];
+            st->rhs[sn] = red[MC + 1];
+            st->en2[sn] = red[MC + 2];
+            st->list[nold] = sn;
+            st->count = nold + 1;
+            st->new_slot = sn;
+        }
+        __syncwarp();
+    }
+    memory_solve_tail(st, mp, M, sm, tr);
 }
 
 // ---------------------------------------------------------------------------
@@ -339,20 +353,103 @@ __device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int c
 }
 
 // ---------------------------------------------------------------------------
-// k_memory: the per-iteration memory pass.  MC >= m_A bounds the number of
-// old columns read (compile-time, so the partial sums stay in registers).
-// mode INIT: only g^0 = u^1 - u^0 is written.
+// Single-LP memory pass, in two kernels.
+//
+// k_memory (every iteration) forms g^k = uh - u, dg = g^k - g^{k-1} and
+// du = u^k - u^{k-1}, writes the new memory column (dg, and du + beta D-hat
+// dg), and sums ||dg||^2, <dg, g^k> and ||du||^2.  Its last block appends the
+// column to the list (dropping the oldest when m_A are held).  The new
+// column's Gram entries with the older columns are formed later, by k_gram,
+// at the first AA attempt that needs them (the safeguard of Alg. 2 passing):
+// until then the column is "stale", and a column that leaves the memory while
+// stale never has them formed.  When the safeguard failed, the iteration ends
+// in k_memory's last block (a PDHG step).
+//
+// k_gram (only when the safeguard passed) forms, in one pass over the memory
+// columns and g^k, the entries <dg_s, dg_t> of every stale column s with every
+// other column t and the right-hand side <dg_t, g^k> of every column, then
+// solves (Alg. 2, or the filters of Alg. 3) in its last block.  Every Gram
+// entry is one dot product of two stored columns, formed once, as in the
+// incremental update of Sec. 5: with an attempt at every iteration k_gram
+// forms one row per iteration; with r failed safeguard tests in between it
+// forms the r rows in one pass instead of r passes, and none in iterations
+// without an attempt.
 // ---------------------------------------------------------------------------
-template <typename V, int MC>
-__global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, int mode) {
+
+// Per-element work of k_memory on W consecutive elements at e0:
+// acc[0] ||dg||^2, acc[1] <dg, g^k>, acc[2] ||du||^2.
+template <typename V, int W>
+__device__ __forceinline__ void push_elems(const Prob<V> &P, int64_t e0, int cur, bool prev_acc,
+                                           V beta, V *DGn, V *Wn, Acc<V> (&acc)[3]) {
+    const V *UPs = reinterpret_cast<const V *>(P.UP);
+    const Pack<V, W> pa = ld_stream<V, W>(UPs + 2 * e0), pb = ld_stream<V, W>(UPs + 2 * e0 + W);
+    const Pack<V, W> gp = ld_stream<V, W>(P.g + e0);
+    const Pack<V, W> dh = ld<V, W>(P.dh + e0);
+    Pack<V, W> wn;
+    if (prev_acc) wn = ld_stream<V, W>(Wn + e0);
+    Pack<V, W> gk, dgk, wk;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const int i0 = 2 * i, i1 = 2 * i + 1;
+        const V c0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
+        const V c1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
+        const V u = cur ? c1 : c0, uh = cur ? c0 : c1;
+        const V g = uh - u;
+        const V dg = g - gp.v[i];
+        const V du = prev_acc ? wn.v[i] : gp.v[i];     // u^k - u^{k-1}
+        gk.v[i] = g;
+        dgk.v[i] = dg;
+        wk.v[i] = du + beta * dh.v[i] * dg;
+        acc[0].add_sq(dg);
+        acc[1].add_prod(dg, g);
+        acc[2].add_sq(du);
+    }
+    st<V, W>(P.g + e0, gk);
+    st<V, W>(DGn + e0, dgk);
+    st<V, W>(Wn + e0, wk);
+}
+
+// Appends the new column (warp 0 of k_memory's last block) and, when the
+// safeguard failed, ends the iteration.  red = {||dg||^2, <dg, g^k>, ||du||^2}.
+static __device__ void push_finalize(DevState *st, const MethodParams &mp, int M, int sn, const double *red,
+                              SolveSmem &sm, const Trace &tr) {
+    const int lane = threadIdx.x & 31;
+    if (M > 0 && lane == 0) {
+        int cnt = st->count;
+        if (cnt == M) {                                 // the oldest column leaves
+            st->stale &= ~(1ull << st->list[0]);
+            for (int i = 1; i < cnt; ++i) st->list[i - 1] = st->list[i];
+            cnt -= 1;
+        }
+        st->list[cnt] = sn;
+        st->count = cnt + 1;
+        st->new_slot = sn;
+        st->G[sn * NSLOT + sn] = red[0];
+        st->rhs[sn] = red[1];
+        st->en2[sn] = red[2];
+        if (cnt > 0) st->stale |= 1ull << sn;           // entries with the older columns pending
+    }
+    __syncwarp();
+    if (M > 0 && st->want_aa) return;                   // k_gram finishes the iteration
+    memory_solve_tail(st, mp, M, sm, tr);
+}
+
+// k_memory: see above.  mode INIT: only g^0 = u^1 - u^0 is written.
+// fin = 1 (iterations without a KKT test): the half-steps' final reduction
+// (||g^k||, the safeguard test; k_finalize's work) runs here, in the last
+// block, before the decisions that need it.  Without a KKT test the iteration
+// cannot stop, so the streaming part may run before that reduction; a NaN/Inf
+// it finds still stops the run before any AA step.
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, int mode, int fin) {
     constexpr int W = 16 / sizeof(V);
     DevState *st = P.st;
     if (st->done | st->error) return;
     const int M = (mp.method == 0) ? 0 : mp.mem;
-    __shared__ int s_old[NSLOT];
-    __shared__ int64_t s_off[NSLOT];
-    __shared__ int s_nold, s_new, s_prev_acc;
-    __shared__ typename Acc<V>::Packed sh[WARPS * (MC + 3)];
+    __shared__ int s_new, s_prev_acc;
+    __shared__ typename Acc<V>::Packed sh[WARPS * 3];
+    __shared__ double red[3];
+    __shared__ SolveSmem sm;
     const int cur = (mode == MODE_INIT) ? 0 : (int)(st->it & 1) ^ 1;
     // the iteration of a primal weight update restarts the memory: a plain
     // step, g^k kept as the previous residual, no column formed across it
@@ -366,8 +463,15 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
                 P.g[e] = comp<V>(pr, 1 - cur) - comp<V>(pr, cur);
             }
         }
-        if (last_block(&st->cnt_ring) && threadIdx.x == 0) {
+        if (!last_block(&st->cnt_ring)) return;
+        if (fin) {
+            finalize_T<V>(P, mp, MODE_ITER, false);
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
             st->count = 0;
+            st->stale = 0ull;
+            st->want_aa = 0;  // a restart takes the plain step
             st->new_slot = 0;
             st->free_slot = 0;
             st->accept = 0;   // u^1 = T u^0 behaves as a PDHG step: du^0 = g^0
@@ -390,72 +494,286 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     }
 
     if (threadIdx.x == 0) {
-        // old columns that stay in the memory after the new one is appended
-        const int cnt = st->count;
-        const int drop = (M > 0 && cnt == M) ? 1 : 0;
-        int t = 0;
-        for (int i = drop; i < cnt; ++i) s_old[t++] = st->list[i];
-        s_nold = t;
         s_new = st->free_slot;
         s_prev_acc = st->accept;
     }
     __syncthreads();
-    if (threadIdx.x < NSLOT) s_off[threadIdx.x] = (int64_t)s_old[threadIdx.x < s_nold ? threadIdx.x : 0] * P.Npad;
-    __syncthreads();
-    const int nold = s_nold, sn = s_new;
+    const int sn = s_new;
     const bool prev_acc = s_prev_acc != 0;
-
-    Acc<V> acc[MC + 3];   // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2
     if (M > 0) {
+        Acc<V> acc[3];
         V *DGn = P.DG + (int64_t)sn * P.Npad;
         V *Wn = P.W + (int64_t)sn * P.Npad;
         const V beta = (V)mp.beta;
         const int64_t NV = P.N / W * W;
         const int64_t stride = (int64_t)gridDim.x * BLOCK;
         for (int64_t e0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) * W; e0 < NV; e0 += stride * W)
-            memory_elems<V, MC, W>(P, e0, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
+            push_elems<V, W>(P, e0, cur, prev_acc, beta, DGn, Wn, acc);
         for (int64_t e = NV + blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N; e += stride)
-            memory_elems<V, MC, 1>(P, e, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
-        // block reduce -> partials
+            push_elems<V, 1>(P, e, cur, prev_acc, beta, DGn, Wn, acc);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-        for (int s = 0; s < MC + 3; ++s) {
-            if (s < nold || s >= MC) {
-                acc[s].warp_allreduce();
-                if (lane == 0) sh[warp * (MC + 3) + s] = acc[s].pack();
-            }
+        for (int j = 0; j < 3; ++j) {
+            acc[j].warp_allreduce();
+            if (lane == 0) sh[warp * 3 + j] = acc[j].pack();
         }
         __syncthreads();
-        for (int s = threadIdx.x; s < MC + 3; s += BLOCK) {
-            if (s < nold || s >= MC) {
-                double v = 0.0;
-                for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * (MC + 3) + s]);
-                P.part3[(int64_t)blockIdx.x * (MC + 3) + s] = v;
-            }
+        if (threadIdx.x < 3) {
+            double v = 0.0;
+            for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * 3 + threadIdx.x]);
+            P.part3[(int64_t)blockIdx.x * 3 + threadIdx.x] = v;
         }
     }
     if (!last_block(&st->cnt_ring)) return;
-
-    // ---- final reduction and the m x m work (one block) -------------------
-    __shared__ double red[MC + 3];
-    __shared__ SolveSmem sm;
+    if (fin) {
+        finalize_T<V>(P, mp, mode, false);
+        __syncthreads();
+        if (*reinterpret_cast<volatile int32_t *>(&st->error)) return;
+    }
     if (M > 0) {
-        // one warp per partial column, lanes striding the blocks, shuffle tree:
-        // a fixed summation order without block-wide barriers
+        // one warp per partial column, lanes striding the blocks: fixed order
         const int wl = threadIdx.x & 31, ww = threadIdx.x >> 5;
-        for (int s = ww; s < MC + 3; s += WARPS) {
-            if (s < nold || s >= MC) {
-                double v = 0.0;
-                for (int b = wl; b < P.grid3; b += 32) v += __ldcg(P.part3 + (int64_t)b * (MC + 3) + s);
+        if (ww < 3) {
+            double v = 0.0;
+            for (int b = wl; b < P.grid3; b += 32) v += __ldcg(P.part3 + (int64_t)b * 3 + ww);
 #pragma unroll
-                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (wl == 0) red[s] = v;
+            for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (wl == 0) red[ww] = v;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x >= 32) return;
+    push_finalize(st, mp, M, sn, red, sm, P.tr);
+}
+
+// k_gram: see above.  The pairs of vectors to multiply (columns by list
+// position 0 .. k-1, and k for g^k) are listed in shared memory.  The block is
+// warp-specialised: warp 0 brings tiles of GRAM_TILE_BYTES of every vector
+// into shared memory with bulk asynchronous copies (cp.async.bulk), each stage
+// completing on its "full" mbarrier, up to GRAM_STAGES tiles ahead; the other
+// GRAM_CWARPS warps multiply, consumer warp c accumulating pairs c, c +
+// GRAM_CWARPS, ... (at most GRAM_PW per warp and pass; more pairs take more
+// passes over the tiles) in float-float pairs (mixed) or FP64, and release a
+// stage by arriving on its "empty" mbarrier.  The elements after the last
+// whole tile are read directly by block 0.  Block partials go to
+// part4[block][pair]; the last block sums them in block order, writes the
+// Gram entries and the right-hand side, and solves.  Every wait on a barrier
+// is bounded: one that gives up sets st->error = 2 (reported by the host),
+// and the block waits (bounded) for its copies in flight before it returns.
+constexpr int GRAM_PW = 16;
+constexpr int GRAM_MAX_OCC = 8;            // resident blocks per SM the Gram pass uses at most
+constexpr int GRAM_MAXPAIRS = MAXM * (MAXM - 1) / 2 + MAXM;
+constexpr int GRAM_TILE_BYTES = 2048;
+constexpr int GRAM_STAGES = 2;
+constexpr int GRAM_CWARPS = WARPS - 1;     // consumer warps (warp 0 produces)
+constexpr int GRAM_WAIT_LIMIT = 1 << 22;   // try_wait polls before a wait gives up
+
+__host__ __device__ constexpr int gram_dyn_smem(int mem) {
+    return GRAM_STAGES * (mem + 1) * GRAM_TILE_BYTES;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(a) : "memory");
+}
+
+// Bounded wait for the phase with parity `parity` of the barrier to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(bar);
+    for (int it = 0; it < GRAM_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    const uint32_t b = (uint32_t)__cvta_generic_to_shared(bar);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(d), "l"(src), "r"(bytes), "r"(b)
+        : "memory");
+}
+
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
+    constexpr int W = 16 / sizeof(V);
+    constexpr int TILE = GRAM_TILE_BYTES / sizeof(V);   // elements per tile
+    constexpr int VPL = TILE / (32 * W);                // 16-byte vectors per lane and tile
+    DevState *st = P.st;
+    if (st->done | st->error) return;
+    if (!st->want_aa || mp.method == 0 || mp.mem == 0) return;
+    extern __shared__ __align__(128) unsigned char gram_smem[];
+    __shared__ int s_k, s_np, s_fail;
+    __shared__ int s_list[NSLOT];
+    __shared__ uint64_t s_stale;
+    __shared__ int16_t s_pa[GRAM_MAXPAIRS], s_pb[GRAM_MAXPAIRS];
+    __shared__ const V *s_vec[NSLOT + 1];
+    __shared__ __align__(8) uint64_t full[GRAM_STAGES], empty[GRAM_STAGES];
+    __shared__ SolveSmem sm;
+    if (threadIdx.x == 0) {
+        s_k = st->count;
+        s_stale = st->stale;
+        s_fail = 0;
+    }
+    if (threadIdx.x < NSLOT) s_list[threadIdx.x] = st->list[threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {                              // the pair list, from shared memory
+        const int k = s_k;
+        const uint64_t stale = s_stale;
+        int np = 0;
+        for (int a = 0; a < k; ++a)
+            for (int b = a + 1; b < k; ++b)
+                if (((stale >> s_list[a]) | (stale >> s_list[b])) & 1ull) {
+                    s_pa[np] = (int16_t)a;
+                    s_pb[np] = (int16_t)b;
+                    ++np;
+                }
+        for (int a = 0; a + 1 < k; ++a) {              // the newest column's <dg, g^k> is known
+            s_pa[np] = (int16_t)a;
+            s_pb[np] = (int16_t)k;
+            ++np;
+        }
+        s_np = np;
+        for (int s2 = 0; s2 < GRAM_STAGES; ++s2) {
+            mbar_init(&full[s2], 1);
+            mbar_init(&empty[s2], GRAM_CWARPS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int k = s_k, np = s_np;
+    if (threadIdx.x < k) s_vec[threadIdx.x] = P.DG + (int64_t)s_list[threadIdx.x] * P.Npad;
+    if (threadIdx.x == k) s_vec[k] = P.g;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t nfull = P.N / TILE;                   // whole tiles, copied in bulk
+    const int64_t mine = nfull > blockIdx.x ? (nfull - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int npass = (np + GRAM_CWARPS * GRAM_PW - 1) / (GRAM_CWARPS * GRAM_PW);
+    const int64_t items = mine * npass;                 // (pass, tile), in order
+    auto stage_ptr = [&](int s2, int v) {
+        return reinterpret_cast<V *>(gram_smem + ((size_t)s2 * (k + 1) + v) * GRAM_TILE_BYTES);
+    };
+
+    if (warp == 0) {
+        // producer: item q into stage q % GRAM_STAGES once its consumers released it
+        if (lane == 0) {
+            for (int64_t q = 0; q < items; ++q) {
+                const int s2 = (int)(q % GRAM_STAGES);
+                if (q >= GRAM_STAGES && !mbar_wait(&empty[s2], (uint32_t)(((q / GRAM_STAGES) - 1) & 1))) {
+                    s_fail = 1;
+                    break;
+                }
+                const int64_t e0 = (blockIdx.x + (q % mine) * gridDim.x) * (int64_t)TILE;
+                mbar_expect_tx(&full[s2], (uint32_t)((k + 1) * GRAM_TILE_BYTES));
+                for (int v = 0; v <= k; ++v)
+                    bulk_g2s(stage_ptr(s2, v), s_vec[v] + e0, GRAM_TILE_BYTES, &full[s2]);
+            }
+            // every copy issued must land before the block may leave
+            const int64_t last = items < GRAM_STAGES ? items : GRAM_STAGES;
+            for (int64_t j = 0; j < last; ++j) {
+                const int64_t q = items - 1 - j;
+                if (!mbar_wait(&full[q % GRAM_STAGES], (uint32_t)((q / GRAM_STAGES) & 1))) s_fail = 1;
+            }
+        }
+    } else {
+        const int cw = warp - 1;
+        for (int pass = 0; pass < npass; ++pass) {
+            const int p0 = pass * GRAM_CWARPS * GRAM_PW;
+            Acc<V> acc[GRAM_PW];
+            for (int64_t i = 0; i < mine; ++i) {
+                const int64_t q = (int64_t)pass * mine + i;
+                const int s2 = (int)(q % GRAM_STAGES);
+                if (!mbar_wait(&full[s2], (uint32_t)((q / GRAM_STAGES) & 1))) {
+                    if (lane == 0) s_fail = 1;
+                    break;
+                }
+#pragma unroll
+                for (int j = 0; j < GRAM_PW; ++j) {
+                    const int p = p0 + cw + j * GRAM_CWARPS;
+                    if (p < np) {
+                        const V *a = stage_ptr(s2, s_pa[p]), *b = stage_ptr(s2, s_pb[p]);
+#pragma unroll
+                        for (int c = 0; c < VPL; ++c) {
+                            const int off = (c * 32 + lane) * W;
+                            const Pack<V, W> x = ld<V, W>(a + off), y = ld<V, W>(b + off);
+#pragma unroll
+                            for (int t = 0; t < W; ++t) acc[j].add_prod(x.v[t], y.v[t]);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s2]);
+            }
+            // the elements after the last whole tile, read directly by block 0
+            if (blockIdx.x == 0) {
+#pragma unroll
+                for (int j = 0; j < GRAM_PW; ++j) {
+                    const int p = p0 + cw + j * GRAM_CWARPS;
+                    if (p < np) {
+                        const V *a = s_vec[s_pa[p]], *b = s_vec[s_pb[p]];
+                        for (int64_t e = nfull * TILE + lane; e < P.N; e += 32) acc[j].add_prod(a[e], b[e]);
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < GRAM_PW; ++j) {
+                const int p = p0 + cw + j * GRAM_CWARPS;
+                if (p < np) {
+                    acc[j].warp_allreduce();
+                    if (lane == 0) P.part4[(int64_t)blockIdx.x * GRAM_MAXPAIRS + p] = acc[j].value();
+                }
+            }
+        }
+    }
+    __syncthreads();
+    if (s_fail) {
+        if (threadIdx.x == 0) st->error = 2;
+        return;
+    }
+    if (!last_block(&st->cnt_gram)) return;
+    // one warp per pair, lanes striding the blocks: fixed order
+    for (int p = warp; p < np; p += WARPS) {
+        double v = 0.0;
+        for (int b = lane; b < P.grid4; b += 32) v += __ldcg(P.part4 + (int64_t)b * GRAM_MAXPAIRS + p);
+#pragma unroll
+        for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) {
+            const int a = s_list[s_pa[p]], bv = s_pb[p];
+            if (bv == k) {
+                st->rhs[a] = v;
+            } else {
+                const int b = s_list[bv];
+                st->G[a * NSLOT + b] = v;
+                st->G[b * NSLOT + a] = v;
             }
         }
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
-    memory_finalize<MC>(st, mp, M, s_old, nold, sn, red, sm, P.tr);
+    if (lane == 0) st->stale = 0ull;
+    __syncwarp();
+    memory_solve_tail(st, mp, mp.mem, sm, P.tr);
 }
 
 // ---------------------------------------------------------------------------

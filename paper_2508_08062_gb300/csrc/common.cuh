@@ -130,7 +130,9 @@ struct DevState {
     int32_t kkt_valid;
     uint32_t cnt_ring;     // last-block counter of the memory pass
     uint32_t cnt_norm;     // last-block counter of the norm kernels
-    double scratch[8];
+    uint64_t stale;        // single LP: slots whose Gram entries with the other columns are pending
+    uint32_t cnt_gram;     // last-block counter of the Gram pass
+    double scratch[8];     // (kept by a reset: ||q||^2, ||c||^2 of the create)
 };
 
 // Safeguard factor (i^k / c_div + 1)^-(1+eps) of Alg. 2 (reading R3), cached
@@ -213,6 +215,8 @@ template <typename V> struct Prob {
     const V *sc_x, *sc_y;         // 1 / Dc (n) and 1 / Dr (m) when the LP is scaled, else null
     double *part1, *part2, *part3;// block partials of the x-step, y-step, memory pass
     int32_t grid1, grid2, grid3;  // grids of those kernels (fixed: deterministic sums)
+    double *part4;                // single LP: block partials of the Gram pass
+    int32_t grid4;
     DevState *st;
     Trace tr;
 };

@@ -431,6 +431,7 @@ static __device__ void push_finalize(DevState *st, const MethodParams &mp, int M
     }
     __syncwarp();
     if (M > 0 && st->want_aa) return;                   // k_gram finishes the iteration
+    if (lane == 0) st->rhs_fresh = 0;                   // rhs lags g^k from here on
     memory_solve_tail(st, mp, M, sm, tr);
 }
 
@@ -471,6 +472,7 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
         if (threadIdx.x == 0) {
             st->count = 0;
             st->stale = 0ull;
+            st->rhs_fresh = 0;
             st->want_aa = 0;  // a restart takes the plain step
             st->new_slot = 0;
             st->free_slot = 0;
@@ -624,7 +626,7 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
     if (st->done | st->error) return;
     if (!st->want_aa || mp.method == 0 || mp.mem == 0) return;
     extern __shared__ __align__(128) unsigned char gram_smem[];
-    __shared__ int s_k, s_np, s_fail;
+    __shared__ int s_k, s_np, s_fail, s_incr;
     __shared__ int s_list[NSLOT];
     __shared__ uint64_t s_stale;
     __shared__ int16_t s_pa[GRAM_MAXPAIRS], s_pb[GRAM_MAXPAIRS];
@@ -641,6 +643,12 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
     if (threadIdx.x == 0) {                              // the pair list, from shared memory
         const int k = s_k;
         const uint64_t stale = s_stale;
+        // The last iteration was an attempt and only the newest column is
+        // stale: its row gives the right-hand side incrementally,
+        // <dg_s, g^k> = <dg_s, g^{k-1}> + <dg_s, dg> (the update of Sec. 5),
+        // so the row is the only pass needed.  Otherwise every column's
+        // <dg_s, g^k> is summed directly.
+        const int incr = st->rhs_fresh && k >= 2 && stale == (1ull << s_list[k - 1]);
         int np = 0;
         for (int a = 0; a < k; ++a)
             for (int b = a + 1; b < k; ++b)
@@ -649,12 +657,14 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
                     s_pb[np] = (int16_t)b;
                     ++np;
                 }
-        for (int a = 0; a + 1 < k; ++a) {              // the newest column's <dg, g^k> is known
-            s_pa[np] = (int16_t)a;
-            s_pb[np] = (int16_t)k;
-            ++np;
-        }
+        if (!incr)
+            for (int a = 0; a + 1 < k; ++a) {          // the newest column's <dg, g^k> is known
+                s_pa[np] = (int16_t)a;
+                s_pb[np] = (int16_t)k;
+                ++np;
+            }
         s_np = np;
+        s_incr = incr;
         for (int s2 = 0; s2 < GRAM_STAGES; ++s2) {
             mbar_init(&full[s2], 1);
             mbar_init(&empty[s2], GRAM_CWARPS);
@@ -766,12 +776,16 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
                 const int b = s_list[bv];
                 st->G[a * NSLOT + b] = v;
                 st->G[b * NSLOT + a] = v;
+                if (s_incr) st->rhs[a] += v;            // (b is the newest column)
             }
         }
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
-    if (lane == 0) st->stale = 0ull;
+    if (lane == 0) {
+        st->stale = 0ull;
+        st->rhs_fresh = 1;
+    }
     __syncwarp();
     memory_solve_tail(st, mp, mp.mem, sm, P.tr);
 }

@@ -306,7 +306,7 @@ def run_ours(args):
     value = whole_job_rate(world, args.steps, t_max)
 
     # per-kernel CUDA-event pass (same loop, instrumented), for the roofline
-    if args.profile_region:              # the region an ncu capture with --profile-from-start off sees
+    if args.profile_region == "timed":   # the region an ncu capture with --profile-from-start off sees
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStart()
     s.profile_kernels(True)
@@ -315,7 +315,7 @@ def run_ours(args):
     cp1 = s.counters()
     prof = s.kernel_profile()
     s.profile_kernels(False)
-    if args.profile_region:
+    if args.profile_region == "timed":
         torch.cuda.synchronize()
         torch.cuda.cudart().cudaProfilerStop()
     acc_p = cp1["aa_steps"] - cp0["aa_steps"]
@@ -376,10 +376,16 @@ def run_ours(args):
             ca1 = s.counters()
             s.set_method(wl["method"], mem=M, D=1e30, eps=1.0)
             s.iterate(ae_warm, tol=0.0, kkt_every=kkt_every)
+            if args.profile_region == "forced":    # every iteration attempts the AA step here
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStart()
             s.profile_kernels(True)
             cq0 = s.counters()
             s.iterate(n_ae, tol=0.0, kkt_every=kkt_every)
             cq1 = s.counters()
+            if args.profile_region == "forced":
+                torch.cuda.synchronize()
+                torch.cuda.cudart().cudaProfilerStop()
         except AAPDHGError as exc:
             aa_every = {"error": str(exc), "note": "safeguard D = 1e30 diverged"}
     if wl["method"] != "pdhg" and aa_every is None:
@@ -1050,8 +1056,11 @@ def main():
                     help="iteration cap of the time-to-1e-4 leg on the large LP")
     ap.add_argument("--precondition", action="store_true",
                     help="Ruiz (10 passes) + Pock-Chambolle diagonal scaling before the step size")
-    ap.add_argument("--profile-region", action="store_true",
-                    help="bracket the per-kernel CUDA-event pass with cudaProfilerStart/Stop")
+    ap.add_argument("--profile-region", nargs="?", const="timed", default=None,
+                    choices=["timed", "forced"],
+                    help="bracket with cudaProfilerStart/Stop the per-kernel CUDA-event pass of "
+                         "the AA loop (timed, the default) or of the pass with the AA step "
+                         "attempted every iteration (forced)")
     ap.add_argument("--primal-weight", type=int, default=0,
                     help="primal weight update every this many iterations (0: off; paper: 3000)")
     ap.add_argument("--batch-max-iters", type=int, default=100000,

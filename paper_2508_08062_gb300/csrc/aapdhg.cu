@@ -472,9 +472,17 @@ int grid_for(aapdhg_t h, int64_t blocks_needed, int occ) {
 // D-hat (mode 1: the Remark on its construction; 0: identity) of the current K.
 template <typename V> void launch_dhat(aapdhg_t h, int mode, cudaStream_t s) {
     Prob<V> &P = prob<V>(h);
-    const int64_t tasks = (int64_t)P.KT.n_long + P.KT.n_slices + P.K.n_long + P.K.n_slices;
+    V *dh = const_cast<V *>(P.dh);
+    const int64_t tasks = (int64_t)P.KT.n_chunks + P.KT.n_slices + P.K.n_chunks + P.K.n_slices;
+    if (mode == 1) {          // the long rows' maxima start at 0
+        if (P.KT.n_long) cudaMemsetAsync(dh, 0, sizeof(V) * P.KT.n_long, s);
+        if (P.K.n_long) cudaMemsetAsync(dh + h->n, 0, sizeof(V) * P.K.n_long, s);
+    }
     k_dhat_sliced<V><<<grid_for(h, (std::max(tasks, h->N / 32) + WARPS - 1) / WARPS, 8), BLOCK, 0, s>>>(
-        P.KT, P.K, h->n, mode, const_cast<V *>(P.dh));
+        P.KT, P.K, h->n, mode, dh);
+    if (mode == 1 && P.KT.n_long + P.K.n_long > 0)
+        k_dhat_long<V><<<grid_for(h, (P.KT.n_long + P.K.n_long + BLOCK - 1) / BLOCK, 4), BLOCK, 0, s>>>(
+            P.KT.n_long, P.K.n_long, h->n, dh);
 }
 
 // Kernel kinds of the instrumentation.

@@ -87,34 +87,48 @@ __global__ void k_dhat(CSRView<V> KT, CSRView<V> K, int32_t n, int32_t m, int mo
 }
 
 // The same D-hat for one LP in the half-steps' layout (rows longest first:
-// rows 0 .. n_long - 1 are long CSR rows, slice q holds rows n_long + 32 q
-// on), one warp task per long row or per SELL slice: a long row is reduced by
-// its warp, a slice by one lane per row with coalesced loads.  |entry| and
-// max are exact in any precision and order, so the result equals k_dhat's.
+// rows 0 .. n_long - 1 are long CSR rows cut into chunks, slice q holds rows
+// n_long + 32 q on).  k_dhat_sliced runs one warp task per chunk or per SELL
+// slice: a chunk's warp folds its max |entry| into its row's entry of dh (an
+// atomic max on the bit pattern, which orders non-negative floats as
+// integers; those entries start at 0), a slice is reduced by one lane per row
+// with coalesced loads and finished at once; k_dhat_long then finishes the
+// long rows.  |entry| and max are exact in any precision and order, so the
+// result equals k_dhat's.
+__device__ __forceinline__ void atomic_max_nonneg(float *p, float v) {
+    atomicMax(reinterpret_cast<unsigned int *>(p), __float_as_uint(v));
+}
+__device__ __forceinline__ void atomic_max_nonneg(double *p, double v) {
+    atomicMax(reinterpret_cast<unsigned long long *>(p), (unsigned long long)__double_as_longlong(v));
+}
+
 template <typename V>
 __device__ __forceinline__ void dhat_task(const CSRView<V> &A, int64_t t, V *out) {
     const int lane = threadIdx.x & 31;
     V mx = V(0);
-    int64_t r;
-    if (t < A.n_long) {
-        r = t;
-        for (int32_t k = A.rp[r] + lane; k < A.rp[r + 1]; k += 32) mx = fmax(mx, fabs(A.val[k]));
+    if (t < A.n_chunks) {
+        const int chunk = (int)t;
+        const int r = __ldg(reinterpret_cast<const int *>(A.chunk_meta + chunk));   // long-row id = row
+        const int c0 = __ldg(A.row_chunk0 + r);
+        const int k0 = __ldg(A.rp + r) + (chunk - c0) * LONG_CHUNK;
+        const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
+        for (int k = k0 + lane; k < k1; k += 32) mx = fmax(mx, fabs(A.val[k]));
 #pragma unroll
         for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-        if (lane != 0) return;
-    } else {
-        const int64_t q = t - A.n_long;
-        r = A.n_long + q * 32 + lane;
-        if (r >= A.rows) return;
-        const int4 meta = A.slice_meta[q];      // offset, width (padding entries are 0)
-        for (int tt = 0; tt < meta.y; ++tt) mx = fmax(mx, fabs(A.sell_val[(int64_t)meta.x + (int64_t)tt * 32 + lane]));
+        if (lane == 0) atomic_max_nonneg(out + r, mx);
+        return;
     }
+    const int64_t q = t - A.n_chunks;
+    const int64_t r = A.n_long + q * 32 + lane;
+    if (r >= A.rows) return;
+    const int4 meta = A.slice_meta[q];          // offset, width (padding entries are 0)
+    for (int tt = 0; tt < meta.y; ++tt) mx = fmax(mx, fabs(A.sell_val[(int64_t)meta.x + (int64_t)tt * 32 + lane]));
     out[r] = (V)sqrt(fmax((double)mx, 1e-10));
 }
 
 template <typename V>
 __global__ void k_dhat_sliced(CSRView<V> KT, CSRView<V> K, int32_t n, int mode, V *dh) {
-    const int64_t tx = (int64_t)KT.n_long + KT.n_slices, ty = (int64_t)K.n_long + K.n_slices;
+    const int64_t tx = (int64_t)KT.n_chunks + KT.n_slices, ty = (int64_t)K.n_chunks + K.n_slices;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t w0 = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5);
     if (mode == 0) {
@@ -126,6 +140,16 @@ __global__ void k_dhat_sliced(CSRView<V> KT, CSRView<V> K, int32_t n, int mode, 
     for (int64_t t = w0; t < tx + ty; t += warps) {
         if (t < tx) dhat_task(KT, t, dh);
         else dhat_task(K, t - tx, dh + n);
+    }
+}
+
+// Long rows: dh = sqrt(max(max |entry|, 1e-10)) from the maxima k_dhat_sliced folded in.
+template <typename V>
+__global__ void k_dhat_long(int32_t lx, int32_t ly, int32_t n, V *dh) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)lx + ly;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e < lx ? e : n + (e - lx);
+        dh[i] = (V)sqrt(fmax((double)dh[i], 1e-10));
     }
 }
 

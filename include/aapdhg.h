@@ -425,6 +425,15 @@ aapdhg_status aapdhg_batch_poll(aapdhg_batch_t h, int32_t *all_stopped);
  * inputs (x: sum(n[p]), y: sum(m[p]); either may be NULL).                   */
 aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y);
 
+/* One problem's current iterate (x: n[p], y: m[p], its caller order), the KKT
+ * quantities of its last test (kkt6, as aapdhg_get_kkt; all 0 before the
+ * first test) and its status row (status6, as aapdhg_batch_get_status), read
+ * from that problem's ranges only; any output may be NULL.  A problem that
+ * stopped keeps its iterate, so this can hand its result back while the others
+ * run (after aapdhg_batch_poll).  p outside 0 .. nprob - 1: AAPDHG_ERR_INVALID. */
+aapdhg_status aapdhg_batch_get_member(aapdhg_batch_t h, int32_t p, double *x, double *y,
+                                      double *kkt6, int64_t *status6);
+
 /* KKT quantities of every problem's current iterate: out6[6p .. 6p+5] as in
  * aapdhg_get_kkt (host array of 6 * nprob).                                  */
 aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6);
@@ -461,10 +470,11 @@ void aapdhg_batch_destroy(aapdhg_batch_t h);
  * the given method and memory, D = 10, eps = 1, eta = 1e-10, beta = 1,
  * c_s = 0.2, kappa = 1e8), each LP with its own tolerance; LPs whose tolerance
  * is below 1e-5 are solved in FP64 cohorts, the others in mixed precision.
- * An LP leaves the GPU when its cohort has finished (every member converged,
- * failed or at the iteration cap); its time of convergence is recorded when
- * the step that observes it ends.  The paper solves one LP at a time; this is
- * its method applied to a stream.
+ * An LP that converged or failed has its result handed back by the step that
+ * observes it (its state and result are then final), while the rest of its
+ * cohort runs on; the cohort's memory is freed when every member has finished
+ * (converged, failed or at the iteration cap).  The paper solves one LP at a
+ * time; this is its method applied to a stream.
  *
  *   create:  method, m_A as aapdhg_set_method; max_cohorts >= 1 running at
  *            once; max_cohort_size >= 1 LPs per cohort; max_iters >= 1 per

@@ -46,7 +46,7 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_batch_set_method", "aapdhg_batch_set_scaling", "aapdhg_batch_set_primal_weight",
            "aapdhg_batch_set_start",
            "aapdhg_batch_reset", "aapdhg_batch_iterate", "aapdhg_batch_get_iterate",
-           "aapdhg_batch_get_kkt", "aapdhg_batch_get_status", "aapdhg_batch_profile_kernels",
+           "aapdhg_batch_get_kkt", "aapdhg_batch_get_member", "aapdhg_batch_get_status", "aapdhg_batch_profile_kernels",
            "aapdhg_batch_get_kernel_profile", "aapdhg_batch_device_bytes",
            "aapdhg_batch_last_error", "aapdhg_batch_destroy")
 NO_STATUS = ("aapdhg_last_error", "aapdhg_destroy", "aapdhg_batch_last_error",
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH):
     L.aapdhg_batch_iterate.argtypes = [vp, i64, f64, i32, C.POINTER(i64)]
     L.aapdhg_batch_get_iterate.argtypes = [vp, vp, vp]
     L.aapdhg_batch_get_kkt.argtypes = [vp, vp]
+    L.aapdhg_batch_get_member.argtypes = [vp, i32, vp, vp, vp, vp]
     L.aapdhg_batch_get_status.argtypes = [vp, vp]
     L.aapdhg_batch_profile_kernels.argtypes = [vp, i32]
     L.aapdhg_batch_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
@@ -531,6 +532,16 @@ class BatchSolver:
         out = np.empty((self.nprob, 6))
         self._check(self._L.aapdhg_batch_get_kkt(self._h, _ptr(out)))
         return out
+
+    def get_member(self, p):
+        """One problem's (x, y), the KKT values of its last test and its status row."""
+        p = int(p)
+        x = np.empty(int(self.xoff[p + 1] - self.xoff[p]))
+        y = np.empty(int(self.yoff[p + 1] - self.yoff[p]))
+        kk = np.empty(6)
+        st = np.empty(6, dtype=np.int64)
+        self._check(self._L.aapdhg_batch_get_member(self._h, p, _ptr(x), _ptr(y), _ptr(kk), _ptr(st)))
+        return x, y, kk, st
 
     def status(self):
         """(nprob, 6) int64: iterations, AA steps, PDHG steps, factorisation

@@ -703,6 +703,47 @@ template <typename V> aapdhg_status bget_iterate(bh_t h, double *x, double *y) {
     return AAPDHG_OK;
 }
 
+// One member's current iterate (caller order) and the KKT values of its last
+// test, read from its own ranges only.
+template <typename V> aapdhg_status bget_member(bh_t h, int32_t p, double *x, double *y, double *kkt6,
+                                                int64_t *st6) {
+    typedef typename Vec2<V>::T V2;
+    Prob<V> &P = bprob<V>(h);
+    const int cur = (int)(h->g & 1);
+    std::vector<V2> ux(h->n[p]), uy(std::max(h->m[p], 1));
+    DevState d;
+    BCK(h, cudaMemcpyAsync(ux.data(), P.UP + h->xoff[p], sizeof(V2) * h->n[p], cudaMemcpyDeviceToHost,
+                           h->stream));
+    if (h->m[p] > 0)
+        BCK(h, cudaMemcpyAsync(uy.data(), P.UP + h->n_tot + h->yoff[p], sizeof(V2) * h->m[p],
+                               cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaMemcpyAsync(&d, h->stb + p, sizeof(DevState), cudaMemcpyDeviceToHost, h->stream));
+    BCK(h, cudaStreamSynchronize(h->stream));
+    const int32_t *px = h->perm_x.data() + h->xcat[p];
+    const int32_t *py = h->perm_y.data() + h->ycat[p];
+    if (x)
+        for (int32_t j = 0; j < h->n[p]; ++j) {
+            const double v = (double)(cur ? ux[j].y : ux[j].x);
+            x[px[j]] = h->scaled ? v * h->dc[h->xoff[p] + j] : v;
+        }
+    if (y)
+        for (int32_t i = 0; i < h->m[p]; ++i) {
+            const double v = (double)(cur ? uy[i].y : uy[i].x);
+            y[py[i]] = h->scaled ? v * h->dr[h->yoff[p] + i] : v;
+        }
+    if (kkt6)
+        for (int k = 0; k < 6; ++k) kkt6[k] = d.kkt[k];
+    if (st6) {
+        st6[0] = d.it;
+        st6[1] = d.n_aa;
+        st6[2] = d.n_pd;
+        st6[3] = d.n_lsfail;
+        st6[4] = d.done != 0;
+        st6[5] = d.error != 0;
+    }
+    return AAPDHG_OK;
+}
+
 template <typename V> aapdhg_status bget_kkt(bh_t h, double *out) {
     blaunch_iteration<V>(h, h->g, MODE_EVAL);
     BCK(h, cudaGetLastError());
@@ -1190,6 +1231,15 @@ aapdhg_status aapdhg_batch_get_iterate(aapdhg_batch_t h, double *x, double *y) {
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     return h->prec == AAPDHG_FP64 ? bget_iterate<double>(h, x, y) : bget_iterate<float>(h, x, y);
+}
+
+aapdhg_status aapdhg_batch_get_member(aapdhg_batch_t h, int32_t p, double *x, double *y,
+                                      double *kkt6, int64_t *status6) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (p < 0 || p >= h->nprob) return bfail(h, AAPDHG_ERR_INVALID, "problem index out of range");
+    return h->prec == AAPDHG_FP64 ? bget_member<double>(h, p, x, y, kkt6, status6)
+                                  : bget_member<float>(h, p, x, y, kkt6, status6);
 }
 
 aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6) {

@@ -11,8 +11,10 @@
 //      tolerance below the mixed-precision limit go to FP64 cohorts;
 //   3. polls every cohort; a member is finished when its KKT residual met its
 //      tolerance (its iterate then stays frozen on the device), failed, or
-//      reached the iteration cap; a cohort whose members are all finished
-//      hands its results back and frees its memory.
+//      reached the iteration cap.  A member that converged or failed hands its
+//      result back at once (read from its own ranges), while the rest of its
+//      cohort runs on; a cohort whose members are all finished hands back the
+//      capped ones and frees its memory.
 // So requests that arrive while others are on the GPU start as soon as
 // memory allows, and the work of all cohorts overlaps on the device (each
 // cohort's kernels are on its own stream).  Every member's iterates, Anderson
@@ -47,6 +49,7 @@ struct Request {
     std::vector<double> x, y;
     double kkt[6] = {0, 0, 0, 0, 0, 0};
     int64_t est_bytes = 0;
+    bool collected = false;       // result already read back
 };
 
 struct Cohort {
@@ -210,6 +213,11 @@ aapdhg_status retire(aapdhg_server_t s, Cohort &co) {
     int64_t xo = 0, yo = 0;
     for (int32_t i = 0; i < k; ++i) {
         Request &r = s->reqs[co.ids[i]];
+        if (r.collected) {
+            xo += r.n;
+            yo += r.m;
+            continue;
+        }
         if (st == AAPDHG_OK) {
             r.x.assign(x.begin() + xo, x.begin() + xo + r.n);
             r.y.assign(y.begin() + yo, y.begin() + yo + r.m);
@@ -351,7 +359,18 @@ aapdhg_status aapdhg_server_step(aapdhg_server_t s, int32_t *running, int32_t *w
             const double t = now_s(s);
             for (size_t j = 0; j < co.ids.size(); ++j) {
                 Request &r = s->reqs[co.ids[j]];
-                if (r.t_done < 0 && (st6[6 * j + 4] || st6[6 * j + 5])) r.t_done = t;
+                if (r.collected || !(st6[6 * j + 4] || st6[6 * j + 5])) continue;
+                if (r.t_done < 0) r.t_done = t;
+                // the member's result now, while its cohort runs on
+                r.x.resize(r.n);
+                r.y.resize(r.m);
+                int64_t row[6];
+                if ((st = aapdhg_batch_get_member(co.b, (int32_t)j, r.x.data(), r.y.data(), r.kkt, row)) !=
+                    AAPDHG_OK)
+                    return sfail(s, st, std::string("member result: ") + aapdhg_batch_last_error(co.b));
+                r.iters = row[0];
+                r.state = row[5] ? AAPDHG_REQ_ERROR : AAPDHG_REQ_CONVERGED;
+                r.collected = true;
             }
         }
         if (stopped || co.iters > s->max_iters) {

@@ -86,6 +86,37 @@ def test_server_results_equal_alone_and_meet_their_tolerance(pw):
         assert o["kkt"] <= tol * (1.05 if tol >= 1e-5 else 1.0 + 1e-6), (tol, o)
 
 
+def test_server_hands_back_a_member_before_its_cohort_finishes():
+    """Two LPs in one cohort, one needing far more iterations: the fast one's
+    result is handed back (state converged, x, y, KKT) by the step that sees it
+    converge, while the other still runs, and it equals the LP solved alone."""
+    from paper_2508_08062_gb300 import Server
+    fast = lpgen.random_lp(60, 150, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=700)
+    slow = lpgen.random_lp(1500, 4000, nnz_per_row=8, frac_ge=0.3, frac_free=0.1,
+                           row_scale_sigma=1.0, seed=703)
+    early = None
+    with Server(method="aa", mem=5, max_cohorts=1, max_cohort_size=2, max_iters=20000) as srv:
+        a = srv.submit(fast, 1e-4)
+        b = srv.submit(slow, 1e-5)
+        for _ in range(20000):
+            running, waiting = srv.step()
+            ra = srv.result(a)
+            if early is None and ra["state"] == "converged":
+                assert srv.result(b)["state"] == "running" and running == 1
+                early = ra
+            if running == 0 and waiting == 0:
+                break
+        final_a, final_b = srv.result(a), srv.result(b)
+    assert early is not None
+    assert final_b["state"] in ("converged", "capped") and final_b["iters"] > early["iters"]
+    assert np.array_equal(early["x"], final_a["x"]) and np.array_equal(early["y"], final_a["y"])
+    assert early["iters"] == final_a["iters"] and early["kkt"] == final_a["kkt"]
+    conv, x, y, its = _alone(fast, 1e-4, 5)
+    assert conv and its == early["iters"]
+    assert np.array_equal(early["x"], x) and np.array_equal(early["y"], y)
+    assert O.kkt(O.OracleLP.from_problem(fast), x, y)["kkt"] <= 1.05e-4
+
+
 def test_server_rejects_what_cannot_fit_and_refuses_malformed_input():
     from paper_2508_08062_gb300 import Server
     good = lpgen.random_lp(120, 300, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=701)

@@ -207,7 +207,8 @@ def kernel_bytes(P, s_v, kind, M, iters, accepted, use_sum, prev_acc):
 # ---------------------------------------------------------------------------
 def time_to_tolerance(args, P_large, rank, stream, barrier):
     """Wall-clock seconds to KKT <= 1e-4 (KKT tested every 64 iterations; the
-    time starts at the first iterate call, after the autotuner) for AA-PDHG and
+    time starts at the first iterate call, after the layout and task-shape
+    tuners) for AA-PDHG and
     plain PDHG on the same GPU in the same precision:
       tiny   200 x 500, FP64, AA m = 5, no scaling (the plain-method workload);
       medium 100k x 300k, mixed, AA m = 10, Ruiz x10 + Pock-Chambolle and the
@@ -233,6 +234,8 @@ def time_to_tolerance(args, P_large, rank, stream, barrier):
                 s.set_scaling(10, True)
             nrm = s.estimate_norm(100, seed=1)
             s.set_steps(0.9 / nrm, 0.9 / nrm)
+            if Q.nnz > 1_000_000:
+                s.autotune_layout()
             s.autotune()
             for meth in ("aa", "pdhg"):
                 s.set_method(meth, mem=mem if meth == "aa" else 0, D=10.0, eps=1.0)
@@ -281,7 +284,8 @@ def run_ours(args):
     if args.primal_weight:
         s.set_primal_weight(period=args.primal_weight)
     kkt_every = 64
-    tuning = s.autotune()        # task shapes of the two half-steps (also done by the first iterate)
+    layout = s.autotune_layout()  # slice width limit and long-row chunk of K', K, with their task shapes
+    tuning = s.autotune()        # task shapes of the two half-steps on that layout
 
     dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
@@ -467,6 +471,9 @@ def run_ours(args):
                        "preconditioning": "Ruiz x10 + Pock-Chambolle" if args.precondition else "none", "method": wl["method"],
                        "primal_weight_period": args.primal_weight,
                        "precision": wl["precision"], "kkt_every": kkt_every,
+                       "layout": {"x": list(layout["x"]), "y": list(layout["y"]),
+                                  "candidates_us": [[c["sell_max"], c["long_chunk"], round(c["x_us"], 1),
+                                                     round(c["y_us"], 1)] for c in layout["candidates"]]},
                        "task_shapes": {"x": tuning["shape_x"], "y": tuning["shape_y"],
                                        "x_us": [round(v, 1) for v in tuning["x_us"]],
                                        "y_us": [round(v, 1) for v in tuning["y_us"]]},

@@ -264,6 +264,30 @@ enum { AAPDHG_TASK_SHAPES = 5 };
 aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us);
 aapdhg_status aapdhg_set_task_shape(aapdhg_t h, int32_t shape_x, int32_t shape_y);
 
+/* Layouts of the two half-steps' matrices K' and K (the SpMVs of eq. pdhg;
+ * the paper has no counterpart).  Rows are numbered longest first; rows of at
+ * most sell_max entries are stored in SELL-32 slices and read one lane per
+ * row; longer rows are cut into chunks of long_chunk entries, one warp per
+ * chunk (32 lanes per row).  The default is sell_max = 32, long_chunk = 1024
+ * for both matrices.  aapdhg_set_layout rebuilds both layouts from layout4 =
+ * {sell_max, long_chunk of K' (the x-step), sell_max, long_chunk of K (the
+ * y-step)}, from the matrices on the device (as scaled), and keeps the run
+ * state; the task shapes are tuned again at the next iterate.  1 <= sell_max
+ * <= 1024, long_chunk a multiple of 32 in [32, 2^20] (AAPDHG_ERR_INVALID
+ * otherwise).  A row's sum runs in a different order under another layout,
+ * so results change by rounding only.  aapdhg_autotune_layout builds each of
+ * AAPDHG_LAYOUT_CANDIDATES layouts in turn for both matrices ((sell_max,
+ * long_chunk) = (32, 1024), (16, 1024), (64, 1024), (128, 1024), (32, 2048),
+ * (64, 2048), (128, 2048), (64, 4096)), tunes the task shapes on it, and keeps
+ * for K' the candidate with the fastest x-step and for K the one with the
+ * fastest y-step; it returns the choice in layout4 (optional) and, in avg_us
+ * (optional, 2 * AAPDHG_LAYOUT_CANDIDATES doubles), the best x-step and
+ * y-step launch time of each candidate.  It changes no run state; it is not
+ * run by aapdhg_iterate.                                                     */
+enum { AAPDHG_LAYOUT_CANDIDATES = 8 };
+aapdhg_status aapdhg_set_layout(aapdhg_t h, const int32_t *layout4);
+aapdhg_status aapdhg_autotune_layout(aapdhg_t h, int32_t *layout4, double *avg_us);
+
 /* KKT residuals of a given point without any device allocation.  The paper
  * has no counterpart to this entry point.  It exists for callers that cannot
  * allocate device memory when they need the residuals: latency-critical loops

@@ -35,7 +35,8 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_get_trace", "aapdhg_get_memory", "aapdhg_profile_kernels",
            "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
-           "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_batch_autotune",
+           "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_set_layout",
+           "aapdhg_autotune_layout", "aapdhg_batch_autotune",
            "aapdhg_set_primal_weight",
            "aapdhg_batch_set_task_shape", "aapdhg_batch_set_tolerances", "aapdhg_batch_launch",
            "aapdhg_batch_poll", "aapdhg_server_create", "aapdhg_server_submit",
@@ -102,6 +103,8 @@ def load(path: str = LIB_PATH):
     L.aapdhg_autotune.argtypes = [vp, vp, vp, vp]
     L.aapdhg_set_primal_weight.argtypes = [vp, i64, f64, f64, i32, f64, f64, f64]
     L.aapdhg_set_task_shape.argtypes = [vp, i32, i32]
+    L.aapdhg_set_layout.argtypes = [vp, vp]
+    L.aapdhg_autotune_layout.argtypes = [vp, vp, vp]
     L.aapdhg_batch_autotune.argtypes = [vp, vp, vp, vp]
     L.aapdhg_batch_set_task_shape.argtypes = [vp, i32, i32]
     L.aapdhg_batch_create.argtypes = [i32] + [vp] * 11 + [i32, vp, C.POINTER(vp)]
@@ -345,17 +348,27 @@ class Solver:
         """Fix the half-step task shapes ((-1, -1): tune again at the next iterate)."""
         self._check(self._L.aapdhg_set_task_shape(self._h, int(shape_x), int(shape_y)))
 
-    def get_memory(self, capacity=32):
-        """The Anderson memory after the last iteration (test hook): Gram matrix and
-        right-hand side (oldest column first), the dG columns (count, n + m) and g^k."""
-        cnt = C.c_int32()
-        N = self.n + self.m
-        gram = np.zeros(capacity * capacity); rhs = np.zeros(capacity)
-        dg = np.zeros((capacity, N)); g = np.zeros(N)
-        self._check(self._L.aapdhg_get_memory(self._h, int(capacity), C.byref(cnt), _ptr(gram),
-                                               _ptr(rhs), _ptr(dg), _ptr(g)))
-        k = cnt.value
-        return dict(count=k, gram=gram[:k * k].reshape(k, k), rhs=rhs[:k], dg=dg[:k], g=g)
+    LAYOUT_CANDIDATES = ((32, 1024), (16, 1024), (64, 1024), (128, 1024), (32, 2048), (64, 2048),
+                         (128, 2048), (64, 4096))
+
+    def set_layout(self, sell_max=32, long_chunk=1024, sell_max_y=None, long_chunk_y=None):
+        """Rebuild the half-steps' matrix layouts: rows up to sell_max entries in
+        SELL-32 slices, longer rows in chunks of long_chunk entries; the first
+        pair for K' (x-step), the second (default: the same) for K (y-step)."""
+        lay = np.array([sell_max, long_chunk, sell_max if sell_max_y is None else sell_max_y,
+                        long_chunk if long_chunk_y is None else long_chunk_y], dtype=np.int32)
+        self._check(self._L.aapdhg_set_layout(self._h, _ptr(lay)))
+
+    def autotune_layout(self):
+        """Time every candidate layout (with its task shapes tuned) and keep the
+        fastest for each matrix; returns the choice and each candidate's best
+        x / y launch (us)."""
+        lay = np.zeros(4, dtype=np.int32)
+        us = np.zeros(2 * len(self.LAYOUT_CANDIDATES))
+        self._check(self._L.aapdhg_autotune_layout(self._h, _ptr(lay), _ptr(us)))
+        return dict(x=(int(lay[0]), int(lay[1])), y=(int(lay[2]), int(lay[3])),
+                    candidates=[dict(sell_max=a, long_chunk=b, x_us=us[2 * i], y_us=us[2 * i + 1])
+                                for i, (a, b) in enumerate(self.LAYOUT_CANDIDATES)])
 
     KERNEL_KINDS = ("xstep", "ystep", "memory", "mix", "gram")
 

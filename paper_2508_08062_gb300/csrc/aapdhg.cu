@@ -56,7 +56,8 @@ void raw_free(void *p) {
     else cudaFree(p);
 }
 
-bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L) {
+bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L,
+                  const LayoutParams &prm) {
     auto len = [&](int32_t r) { return A.rp[r + 1] - A.rp[r]; };
     struct Slice { int32_t row0, rows, pid, width; };
     std::vector<int32_t> long_rows, long_pid;
@@ -64,16 +65,17 @@ bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost 
     for (const RowSeg &sg : segs) {
         int32_t r = sg.row0;
         const int32_t end = sg.row0 + sg.rows;
-        for (; r < end && len(r) > SELL_MAX; ++r) {
+        for (; r < end && len(r) > prm.sell_max; ++r) {
             long_rows.push_back(r);
             long_pid.push_back(sg.pid);
         }
         for (; r < end; r += 32) sl.push_back({r, std::min(32, end - r), sg.pid, len(r)});
     }
     L.n_long = (int32_t)long_rows.size();
+    L.long_chunk = prm.long_chunk;
     L.row_chunk0.assign(L.n_long + 1, 0);
     for (int32_t lr = 0; lr < L.n_long; ++lr) {
-        const int32_t nch = (len(long_rows[lr]) + LONG_CHUNK - 1) / LONG_CHUNK;
+        const int32_t nch = (len(long_rows[lr]) + prm.long_chunk - 1) / prm.long_chunk;
         L.row_chunk0[lr + 1] = L.row_chunk0[lr] + nch;
         for (int32_t c = 0; c < nch; ++c) L.chunk_meta.push_back(make_int4(long_rows[lr], lr, long_pid[lr], 0));
     }
@@ -363,6 +365,11 @@ struct aapdhg_s {
     bool tuned = false, autotune = true;
     // time limit of a run (the paper's one-hour cap); 0: none
     double time_limit = 0.0, time_used = 0.0;
+    // layouts of K' and K (slice width limit, long-row chunk) and the device
+    // allocations of their layout parts, by matrix (0: K', 1: K)
+    LayoutParams lay[2];
+    std::vector<void *> lay_ptrs[2];
+    double lay_us[2 * AAPDHG_LAYOUT_CANDIDATES] = {};
     int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
     double tune_us[2 * NSHAPE] = {};
     // primal weight update (off when pw_period = 0)
@@ -518,6 +525,24 @@ void collect_marks(aapdhg_t h) {
     h->ev_kind.clear();
 }
 
+// Fixed grids of the half-steps per task shape (deterministic reductions),
+// sized for the common (non-KKT) variants, all of whose blocks are resident;
+// a KKT launch (one in kkt_every) may run a short second wave.
+template <typename V> void half_step_grids(aapdhg_t h) {
+    Prob<V> &P = prob<V>(h);
+    const int occx[NSHAPE] = {occupancy(k_xstep<V, false, 0>), occupancy(k_xstep<V, false, 1>),
+                              occupancy(k_xstep<V, false, 2>), occupancy(k_xstep<V, false, 3>),
+                              occupancy(k_xstep<V, false, 4>)};
+    const int occy[NSHAPE] = {occupancy(k_ystep<V, false, 0>), occupancy(k_ystep<V, false, 1>),
+                              occupancy(k_ystep<V, false, 2>), occupancy(k_ystep<V, false, 3>),
+                              occupancy(k_ystep<V, false, 4>)};
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        const int g = task_shape(sh).g;
+        h->gridx[sh] = grid_for(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
+        h->gridy[sh] = grid_for(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
+    }
+}
+
 template <typename V>
 aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, const int8_t *sense,
                            const double *q, const double *c, const double *lb, const double *ub) {
@@ -531,13 +556,20 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     P.N = N;
     P.Npad = h->Npad;
 
-    auto mk_csr = [&](const HostCSR &A, CSRView<V> &view) {
+    auto mk_csr = [&](const HostCSR &A, CSRView<V> &view, int which) {
         LayoutHost L;
-        if (!build_layout(A, {RowSeg{0, A.rows, 0}}, L)) { ok = false; return; }
-        if (!upload_csr<V>(A, L, view, [&](size_t b) { return dev_alloc(h, b); }, h->stream)) ok = false;
+        if (!build_layout(A, {RowSeg{0, A.rows, 0}}, L, h->lay[which])) { ok = false; return; }
+        if (!upload_matrix<V>(A, view, [&](size_t b) { return dev_alloc(h, b); }, h->stream)) ok = false;
+        std::vector<void *> &rec = h->lay_ptrs[which];
+        auto track = [&](size_t b) {
+            void *p = dev_alloc(h, b);
+            if (p) rec.push_back(p);
+            return p;
+        };
+        if (!upload_layout<V>(L, view, track, h->stream)) ok = false;
     };
-    mk_csr(KT, P.KT);
-    mk_csr(K, P.K);
+    mk_csr(KT, P.KT, 0);
+    mk_csr(K, P.K, 1);
     (void)Z;
 
     // vectors in internal order
@@ -564,24 +596,11 @@ aapdhg_status setup_device(aapdhg_t h, const HostCSR &K, const HostCSR &KT, cons
     if (!P.UP || !P.dh || !P.g) ok = false;
     h->d_UP = P.UP;
 
-    // fixed grids per task shape (deterministic reductions), sized for the
-    // common (non-KKT) variants, all of whose blocks are resident; a KKT
-    // launch (one in kkt_every) may run a short second wave
     int occ3 = 0;
-    const int occx[NSHAPE] = {occupancy(k_xstep<V, false, 0>), occupancy(k_xstep<V, false, 1>),
-                              occupancy(k_xstep<V, false, 2>), occupancy(k_xstep<V, false, 3>),
-                              occupancy(k_xstep<V, false, 4>)};
-    const int occy[NSHAPE] = {occupancy(k_ystep<V, false, 0>), occupancy(k_ystep<V, false, 1>),
-                              occupancy(k_ystep<V, false, 2>), occupancy(k_ystep<V, false, 3>),
-                              occupancy(k_ystep<V, false, 4>)};
-    int gmax1 = 1, gmax2 = 1;
-    for (int sh = 0; sh < NSHAPE; ++sh) {
-        const int g = task_shape(sh).g;
-        h->gridx[sh] = grid_for(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
-        h->gridy[sh] = grid_for(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
-        gmax1 = std::max(gmax1, h->gridx[sh]);
-        gmax2 = std::max(gmax2, h->gridy[sh]);
-    }
+    half_step_grids<V>(h);
+    // partial-sum buffers for any grid of resident blocks (a later layout may
+    // need more blocks than this one)
+    const int gmax1 = h->sm_count * 8, gmax2 = h->sm_count * 8;
     P.grid1 = h->gridx[0];
     P.grid2 = h->gridy[0];
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ3, k_memory<V>, BLOCK, 0);
@@ -814,6 +833,115 @@ template <typename V> aapdhg_status autotune_t(aapdhg_t h) {
     h->tuned = true;
     drop_graphs(h);
     return AAPDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Layout of K' and K: the slice width limit (rows up to it go to SELL-32
+// slices, one lane per row) and the entries per warp task of a longer row.
+// ---------------------------------------------------------------------------
+void dev_free_ptrs(aapdhg_t h, const std::vector<void *> &ptrs) {
+    for (void *p : ptrs)
+        for (size_t i = 0; i < h->allocs.size(); ++i)
+            if (h->allocs[i].p == p) {
+                h->bytes -= (int64_t)h->allocs[i].bytes;
+                raw_free(p);
+                h->allocs.erase(h->allocs.begin() + (long)i);
+                break;
+            }
+}
+
+// The internal CSR of a matrix as the device holds it (in the iterate
+// precision; scaled when the LP was scaled).
+template <typename V> aapdhg_status download_csr(aapdhg_t h, const CSRView<V> &v, int64_t nnz, HostCSR &A) {
+    A.rows = v.rows;
+    A.rp.resize((size_t)v.rows + 1);
+    A.ci.resize((size_t)nnz);
+    A.val.resize((size_t)nnz);
+    std::vector<V> tmp((size_t)std::max<int64_t>(nnz, 1));
+    CK(h, cudaMemcpyAsync(A.rp.data(), v.rp, sizeof(int32_t) * ((size_t)v.rows + 1), cudaMemcpyDeviceToHost,
+                          h->stream));
+    if (nnz > 0) {
+        CK(h, cudaMemcpyAsync(A.ci.data(), v.ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, h->stream));
+        CK(h, cudaMemcpyAsync(tmp.data(), v.val, sizeof(V) * (size_t)nnz, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    for (int64_t k = 0; k < nnz; ++k) A.val[k] = (double)tmp[k];
+    return AAPDHG_OK;
+}
+
+// Rebuild the layouts of K' (prm[0]) and K (prm[1]); the run state is kept,
+// the task shapes are tuned again at the next iterate.
+template <typename V> aapdhg_status set_layout_t(aapdhg_t h, const LayoutParams (&prm)[2]) {
+    Prob<V> &P = prob<V>(h);
+    CK(h, cudaStreamSynchronize(h->stream));
+    HostCSR A[2];
+    aapdhg_status s = download_csr<V>(h, P.KT, h->nnz, A[0]);
+    if (s == AAPDHG_OK) s = download_csr<V>(h, P.K, h->nnz, A[1]);
+    if (s != AAPDHG_OK) return s;
+    CSRView<V> nv[2] = {P.KT, P.K};
+    std::vector<void *> rec[2];
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w) {
+        LayoutHost L;
+        if (!build_layout(A[w], {RowSeg{0, A[w].rows, 0}}, L, prm[w])) { ok = false; break; }
+        auto track = [&](size_t b) {
+            void *p = dev_alloc(h, b);
+            if (p) rec[w].push_back(p);
+            return p;
+        };
+        if (!upload_layout<V>(L, nv[w], track, h->stream)) ok = false;
+    }
+    if (!ok) {
+        dev_free_ptrs(h, rec[0]);
+        dev_free_ptrs(h, rec[1]);
+        return fail(h, AAPDHG_ERR_OOM, "layout: device allocation or copy failed");
+    }
+    dev_free_ptrs(h, h->lay_ptrs[0]);
+    dev_free_ptrs(h, h->lay_ptrs[1]);
+    h->lay_ptrs[0] = rec[0];
+    h->lay_ptrs[1] = rec[1];
+    P.KT = nv[0];
+    P.K = nv[1];
+    h->lay[0] = prm[0];
+    h->lay[1] = prm[1];
+    half_step_grids<V>(h);
+    set_shapes(h, 0, 0);
+    h->tuned = false;
+    drop_graphs(h);
+    return AAPDHG_OK;
+}
+
+// Layout candidates of the layout tuner: slice width limit, long-row chunk.
+const LayoutParams kLayoutCand[AAPDHG_LAYOUT_CANDIDATES] = {{32, 1024}, {16, 1024}, {64, 1024},
+                                                            {128, 1024}, {32, 2048}, {64, 2048},
+                                                            {128, 2048}, {64, 4096}};
+
+// Every candidate layout (the same for both matrices), with the task shapes
+// tuned on it.  The x-step reads only K' and the y-step only K, so K' keeps
+// the candidate with the fastest x-step and K the one with the fastest
+// y-step.
+template <typename V> aapdhg_status autotune_layout_t(aapdhg_t h) {
+    double bestx = INFINITY, besty = INFINITY;
+    int bx_i = 0, by_i = 0;
+    for (int c = 0; c < AAPDHG_LAYOUT_CANDIDATES; ++c) {
+        const LayoutParams both[2] = {kLayoutCand[c], kLayoutCand[c]};
+        aapdhg_status s = set_layout_t<V>(h, both);
+        if (s == AAPDHG_OK) s = autotune_t<V>(h);
+        if (s != AAPDHG_OK) return s;
+        double bx = INFINITY, by = INFINITY;
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+            bx = std::min(bx, h->tune_us[sh]);
+            by = std::min(by, h->tune_us[NSHAPE + sh]);
+        }
+        h->lay_us[2 * c] = bx;
+        h->lay_us[2 * c + 1] = by;
+        if (bx < bestx) { bestx = bx; bx_i = c; }
+        if (by < besty) { besty = by; by_i = c; }
+    }
+    const LayoutParams chosen[2] = {kLayoutCand[bx_i], kLayoutCand[by_i]};
+    aapdhg_status s = set_layout_t<V>(h, chosen);
+    if (s == AAPDHG_OK) s = autotune_t<V>(h);
+    return s;
 }
 
 template <typename V> void launch_memory_any(aapdhg_t h, int mode, int fin) {
@@ -1372,6 +1500,37 @@ aapdhg_status aapdhg_get_iterate(aapdhg_t h, double *x, double *y) {
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     return h->prec == AAPDHG_FP64 ? get_iterate_t<double>(h, x, y) : get_iterate_t<float>(h, x, y);
+}
+
+aapdhg_status aapdhg_set_layout(aapdhg_t h, const int32_t *layout4) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!layout4) return fail(h, AAPDHG_ERR_INVALID, "layout4 is NULL");
+    LayoutParams prm[2];
+    for (int w = 0; w < 2; ++w) {
+        const int32_t sm = layout4[2 * w], lc = layout4[2 * w + 1];
+        if (sm < 1 || sm > 1024 || lc < 32 || lc > (1 << 20) || lc % 32)
+            return fail(h, AAPDHG_ERR_INVALID,
+                        "layout: 1 <= sell_max <= 1024, long_chunk a multiple of 32 in [32, 2^20]");
+        prm[w].sell_max = sm;
+        prm[w].long_chunk = lc;
+    }
+    return h->prec == AAPDHG_FP64 ? set_layout_t<double>(h, prm) : set_layout_t<float>(h, prm);
+}
+
+aapdhg_status aapdhg_autotune_layout(aapdhg_t h, int32_t *layout4, double *avg_us) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? autotune_layout_t<double>(h) : autotune_layout_t<float>(h);
+    if (s != AAPDHG_OK) return s;
+    if (layout4) {
+        layout4[0] = h->lay[0].sell_max;
+        layout4[1] = h->lay[0].long_chunk;
+        layout4[2] = h->lay[1].sell_max;
+        layout4[3] = h->lay[1].long_chunk;
+    }
+    if (avg_us) for (int k = 0; k < 2 * AAPDHG_LAYOUT_CANDIDATES; ++k) avg_us[k] = h->lay_us[k];
+    return AAPDHG_OK;
 }
 
 aapdhg_status aapdhg_set_time_limit(aapdhg_t h, double seconds) {

@@ -9,8 +9,8 @@ constexpr int MAXM = 32;            // largest Anderson memory m_A
 constexpr int NSLOT = MAXM + 1;     // ring slots: m_A columns + one slot for the next du
 constexpr int BLOCK = 256;          // threads per block of the streaming kernels
 constexpr int WARPS = BLOCK / 32;
-constexpr int LONG_CHUNK = 1024;    // entries per warp task of a long row
-constexpr int SELL_MAX = 32;        // rows up to this length go to SELL-32 slices
+constexpr int LONG_CHUNK = 1024;    // default entries per warp task of a long row
+constexpr int SELL_MAX = 32;        // default: rows up to this length go to SELL-32 slices
 constexpr int LOADS = 8;            // independent loads a lane keeps in flight
 constexpr int SLICES_PER_TASK = 2;  // SELL slices one warp reads in lockstep
 
@@ -168,10 +168,10 @@ struct Trace {
 };
 
 // One sparse matrix (K or K') with rows renumbered longest first, in two parts:
-//  - n_long rows longer than SELL_MAX entries ("long rows", numbered by a
-//    long-row id): CSR, cut into chunks of at most LONG_CHUNK entries, one
-//    warp task per chunk (a row with several chunks is finished by the warp
-//    whose chunk arrives last);
+//  - n_long rows longer than the layout's slice width limit (SELL_MAX by
+//    default; "long rows", numbered by a long-row id): CSR, cut into chunks of
+//    at most long_chunk entries, one warp task per chunk (a row with several
+//    chunks is finished by the warp whose chunk arrives last);
 //  - the other rows: SELL-32 slices of up to 32 consecutive rows stored
 //    column by column (entry t of the rows contiguous), padded with zero
 //    entries (column 0, value 0) to the slice's longest row; one warp task
@@ -194,6 +194,7 @@ template <typename V> struct CSRView {
     const V *sell_val;
     V *chunk_part;                // n_chunks * 2 partial sums of split rows
     uint32_t *chunk_cnt;          // arrival counters by long-row id (self-resetting)
+    int32_t long_chunk;           // entries per warp task of a long row (the layout's)
     __host__ __device__ int64_t ntasks(int g = SLICES_PER_TASK) const {
         return (int64_t)n_chunks + (n_slices + g - 1) / g;
     }

@@ -83,8 +83,16 @@ struct RowSeg {
 
 // Device-side tables of one matrix built on the host: chunk tables of the long
 // rows and the SELL-32 slices of the others.
+// Layout parameters: rows longer than sell_max entries are long rows, cut
+// into chunks of long_chunk entries (a multiple of 32).
+struct LayoutParams {
+    int32_t sell_max = aap::SELL_MAX;
+    int32_t long_chunk = aap::LONG_CHUNK;
+};
+
 struct LayoutHost {
     int32_t n_long = 0, n_chunks = 0, n_slices = 0;
+    int32_t long_chunk = aap::LONG_CHUNK;
     std::vector<int4> chunk_meta;          // (row, long-row id, problem, 0)
     std::vector<int32_t> row_chunk0;       // long-row id -> first chunk
     std::vector<int4> slice_meta;          // (offset, width, first row, rows | problem << 6)
@@ -93,11 +101,13 @@ struct LayoutHost {
 };
 
 // Layout of A whose rows form the segments `segs` (each longest first): the
-// leading rows of a segment longer than SELL_MAX become long rows, the rest
-// slices of up to 32 rows that never cross a segment.  Slices are ordered by
-// width, widest first, across all segments (stable, so a single segment keeps
-// its row order).  Returns false when the SELL storage would pass 2^31 entries.
-bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L);
+// leading rows of a segment longer than prm.sell_max become long rows, the
+// rest slices of up to 32 rows that never cross a segment.  Slices are ordered
+// by width, widest first, across all segments (stable, so a single segment
+// keeps its row order).  Returns false when the SELL storage would pass 2^31
+// entries.
+bool build_layout(const HostCSR &A, const std::vector<RowSeg> &segs, LayoutHost &L,
+                  const LayoutParams &prm = LayoutParams());
 
 // Internal CSR of K (rows renumbered longest-first, columns mapped to the
 // internal variable order) and of K' (likewise), column indices ascending
@@ -117,11 +127,12 @@ std::string validate_lp(int32_t m, int32_t n, int64_t nnz, const int64_t *rp, co
 void *raw_alloc(size_t bytes);
 void raw_free(void *p);
 
-// Upload A and its layout into `view` (values rounded to V); `alloc(bytes)`
-// returns tracked device memory.  Synchronises `s` (the sources are pageable).
+// Upload the layout L of a matrix into `view` (values rounded to V): chunk
+// and slice tables, the SELL copy, and the split rows' partial sums and
+// counters; `alloc(bytes)` returns tracked device memory.  Synchronises `s`
+// (the sources are pageable).
 template <typename V, class Alloc>
-bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Alloc &&alloc,
-                cudaStream_t s) {
+bool upload_layout(const LayoutHost &L, aap::CSRView<V> &view, Alloc &&alloc, cudaStream_t s) {
     bool ok = true;
     auto put = [&](const auto *src, size_t count) {
         typedef std::remove_cv_t<std::remove_pointer_t<decltype(src)>> T;
@@ -131,22 +142,15 @@ bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Al
             ok = false;
         return d;
     };
-    auto to_v = [](const auto &a) {
-        std::vector<V> o(a.size());
-        run_ranges(even_cuts((int64_t)a.size(), host_threads((int64_t)a.size())),
-                   [&](int, int64_t lo, int64_t hi) {
-                       for (int64_t i = lo; i < hi; ++i) o[i] = (V)a[i];
-                   });
-        return o;
-    };
-    view.rows = A.rows;
-    view.rp = put(A.rp.data(), A.rp.size());
-    view.ci = put(A.ci.data(), A.ci.size());
-    const std::vector<V> v = to_v(A.val), sv = to_v(L.sell_val);
-    view.val = put(v.data(), v.size());
+    std::vector<V> sv(L.sell_val.size());
+    run_ranges(even_cuts((int64_t)sv.size(), host_threads((int64_t)sv.size())),
+               [&](int, int64_t lo, int64_t hi) {
+                   for (int64_t i = lo; i < hi; ++i) sv[i] = (V)L.sell_val[i];
+               });
     view.n_long = L.n_long;
     view.n_chunks = L.n_chunks;
     view.n_slices = L.n_slices;
+    view.long_chunk = L.long_chunk;
     view.chunk_meta = put(L.chunk_meta.data(), L.chunk_meta.size());
     view.row_chunk0 = put(L.row_chunk0.data(), L.row_chunk0.size());
     view.slice_meta = put(L.slice_meta.data(), L.slice_meta.size());
@@ -161,4 +165,37 @@ bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Al
     return ok;
 }
 
+// Upload A's CSR (values rounded to V) into `view`.
+template <typename V, class Alloc>
+bool upload_matrix(const HostCSR &A, aap::CSRView<V> &view, Alloc &&alloc, cudaStream_t s) {
+    bool ok = true;
+    auto put = [&](const auto *src, size_t count) {
+        typedef std::remove_cv_t<std::remove_pointer_t<decltype(src)>> T;
+        T *d = (T *)alloc(sizeof(T) * std::max<size_t>(count, 1));
+        if (!d) { ok = false; return (T *)nullptr; }
+        if (count && cudaMemcpyAsync(d, src, sizeof(T) * count, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            ok = false;
+        return d;
+    };
+    std::vector<V> v(A.val.size());
+    run_ranges(even_cuts((int64_t)v.size(), host_threads((int64_t)v.size())),
+               [&](int, int64_t lo, int64_t hi) {
+                   for (int64_t i = lo; i < hi; ++i) v[i] = (V)A.val[i];
+               });
+    view.rows = A.rows;
+    view.rp = put(A.rp.data(), A.rp.size());
+    view.ci = put(A.ci.data(), A.ci.size());
+    view.val = put(v.data(), v.size());
+    if (cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+    return ok;
+}
+
+// Upload A (its CSR, values rounded to V) and its layout into `view`.
+template <typename V, class Alloc>
+bool upload_csr(const HostCSR &A, const LayoutHost &L, aap::CSRView<V> &view, Alloc &&alloc,
+                cudaStream_t s) {
+    const bool a = upload_matrix<V>(A, view, alloc, s);
+    const bool b = upload_layout<V>(L, view, alloc, s);
+    return a && b;
+}
 }  // namespace aaph

@@ -110,8 +110,8 @@ __device__ __forceinline__ void dhat_task(const CSRView<V> &A, int64_t t, V *out
         const int chunk = (int)t;
         const int r = __ldg(reinterpret_cast<const int *>(A.chunk_meta + chunk));   // long-row id = row
         const int c0 = __ldg(A.row_chunk0 + r);
-        const int k0 = __ldg(A.rp + r) + (chunk - c0) * LONG_CHUNK;
-        const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
+        const int k0 = __ldg(A.rp + r) + (chunk - c0) * A.long_chunk;
+        const int k1 = min(k0 + A.long_chunk, __ldg(A.rp + r + 1));
         for (int k = k0 + lane; k < k1; k += 32) mx = fmax(mx, fabs(A.val[k]));
 #pragma unroll
         for (int o = 16; o; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));

@@ -57,8 +57,8 @@ __device__ __forceinline__ void run_task(const CSRView<V> &A, int64_t t, Gather 
         if (epi.skip(cm.z)) return;
         const int c0 = __ldg(A.row_chunk0 + lr);
         const int nch = __ldg(A.row_chunk0 + lr + 1) - c0;
-        const int k0 = __ldg(A.rp + r) + (chunk - c0) * LONG_CHUNK;
-        const int k1 = min(k0 + LONG_CHUNK, __ldg(A.rp + r + 1));
+        const int k0 = __ldg(A.rp + r) + (chunk - c0) * A.long_chunk;
+        const int k1 = min(k0 + A.long_chunk, __ldg(A.rp + r + 1));
         Pre pre;
         if (nch == 1 && lane == 0) pre = epi.pre(r, cm.z);
         for (int kb = k0 + lane; kb < k1; kb += 32 * LD) {

@@ -328,6 +328,62 @@ def test_task_shapes_give_identical_iterates(prec):
             s.set_task_shape(5, 0)
 
 
+@pytest.mark.parametrize("layout", [(16, 1024), (64, 512), (128, 2048), (1, 32), (64, 4096, 16, 64)])
+def test_fp64_iterates_match_oracle_under_other_layouts(layout):
+    """Rows move between the SELL slices (one lane per row) and the long-row
+    chunks (a warp per chunk) with the slice width limit, and long rows split
+    at other points with the chunk length: the sums run in another order, so
+    the FP64 iterates must still follow the oracle within 1e-9, with the same
+    branches.  (1, 32): every row but the empty ones is a long row, in
+    one-warp chunks of 32 entries.  (64, 4096, 16, 64): K' and K in different
+    layouts."""
+    P = _with_long_row_and_column(5)
+    tau, sig = _steps(P)
+    prm = O.Params(tau=tau, sigma=sig, method=1, mem=8)
+    ref = O.solve(O.OracleLP.from_problem(P), prm, ITERS, trace=True, rec_len=ITERS + 1)
+    with _solver(P) as s:
+        s.set_layout(*layout)
+        s.set_steps(tau, sig)
+        s.set_method("aa", mem=8)
+        s.set_trace(ITERS)
+        s.iterate(0)
+        for k in range(ITERS + 1):
+            x, y = s.get_iterate()
+            r = ref.rec_u[k]
+            err = np.linalg.norm(np.concatenate([x, y]) - r) / np.linalg.norm(r)
+            assert err <= FP64_TOL, (layout, k, err)
+            if k < ITERS:
+                s.iterate(1)
+        tr = s.get_trace()
+    assert np.array_equal(tr["branch"][:ITERS], ref.branch[:ITERS])
+
+
+def test_layout_autotuner_keeps_a_candidate_and_the_results():
+    P = _with_long_row_and_column(6)
+    tau, sig = _steps(P)
+    with _solver(P, "mixed") as s:
+        s.set_steps(tau, sig)
+        s.set_method("aa", mem=5)
+        s.iterate(30)
+        x0, y0 = s.get_iterate()
+        t = s.autotune_layout()                 # the run state is kept
+        assert t["x"] in s.LAYOUT_CANDIDATES and t["y"] in s.LAYOUT_CANDIDATES
+        bx = min(c["x_us"] for c in t["candidates"])
+        by = min(c["y_us"] for c in t["candidates"])
+        assert [c["x_us"] for c in t["candidates"] if (c["sell_max"], c["long_chunk"]) == t["x"]][0] == bx
+        assert [c["y_us"] for c in t["candidates"] if (c["sell_max"], c["long_chunk"]) == t["y"]][0] == by
+        assert all(c["x_us"] > 0 and c["y_us"] > 0 for c in t["candidates"])
+        x1, y1 = s.get_iterate()
+        assert np.array_equal(x0, x1) and np.array_equal(y0, y1)
+        k0 = s.get_kkt()["kkt"]
+        s.iterate(3000)                         # the run goes on under the chosen layout
+        assert s.counters()["iters"] == 3030
+        assert np.isfinite(s.get_kkt()["kkt"]) and s.get_kkt()["kkt"] < k0
+        from paper_2508_08062_gb300 import AAPDHGError
+        with pytest.raises(AAPDHGError):
+            s.set_layout(32, 100)               # not a multiple of 32
+
+
 # --------------------------------------------------------------------------
 # Primal weight update with memory reset and D-hat re-blend (readings R13-R15)
 # --------------------------------------------------------------------------

@@ -702,9 +702,9 @@ def run_batch(args):
     acc = int(st2[:, 1].sum())
     kern = {}
     for kind, d in prof.items():
-        if not d["launches"] or kind in ("kkt", "gram"):
+        if not d["launches"] or kind == "kkt":
             continue
-        bts = kernel_bytes(PK, 4, kind, M, d["launches"], 0, 0, 0) if kind != "mix" else None
+        bts = kernel_bytes(PK, 4, kind, M, d["launches"], 0, 0, 0) if kind not in ("mix", "gram") else None
         gbs = bts / (d["total_ms"] / 1e3) / 1e9 if bts else None
         kern[kind] = dict(launches=d["launches"], avg_us=1e3 * d["total_ms"] / d["launches"],
                           alg_bytes_per_launch=(bts / d["launches"]) if bts else None, gbs=gbs,

@@ -194,9 +194,8 @@ aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double 
                                double *kkt, int32_t *mk);
 
 /* Test hook: the Anderson memory of Alg. 2 as the device holds it after the
- * last iteration k (the columns of dG^{k-m_k} and the incremental Gram matrix
- * of Sec. 5).  *count (optional) receives the number of columns c; gram
- * (c x c, row-major) = <dg_a, dg_b> and rhs (c) = <dg_a, g^k>, columns oldest
+ * last iteration k (the columns of dG^{k-m_k} and their Gram matrix).
+ * *count (optional) receives the number of columns c; gram (c x c, row-major) = <dg_a, dg_b> and rhs (c) = <dg_a, g^k>, columns oldest
  * first, as accumulated on the device (FP64, or float-float pairs summed in
  * FP64 in mixed mode).  The device forms a new column's entries with the
  * other columns, and the right-hand side, at the next AA attempt (an

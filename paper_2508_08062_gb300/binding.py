@@ -348,6 +348,18 @@ class Solver:
         """Fix the half-step task shapes ((-1, -1): tune again at the next iterate)."""
         self._check(self._L.aapdhg_set_task_shape(self._h, int(shape_x), int(shape_y)))
 
+    def get_memory(self, capacity=32):
+        """The Anderson memory after the last iteration (test hook): Gram matrix and
+        right-hand side (oldest column first), the dG columns (count, n + m) and g^k."""
+        cnt = C.c_int32()
+        N = self.n + self.m
+        gram = np.zeros(capacity * capacity); rhs = np.zeros(capacity)
+        dg = np.zeros((capacity, N)); g = np.zeros(N)
+        self._check(self._L.aapdhg_get_memory(self._h, int(capacity), C.byref(cnt), _ptr(gram),
+                                               _ptr(rhs), _ptr(dg), _ptr(g)))
+        k = cnt.value
+        return dict(count=k, gram=gram[:k * k].reshape(k, k), rhs=rhs[:k], dg=dg[:k], g=g)
+
     LAYOUT_CANDIDATES = ((32, 1024), (16, 1024), (64, 1024), (128, 1024), (32, 2048), (64, 2048),
                          (128, 2048), (64, 4096))
 

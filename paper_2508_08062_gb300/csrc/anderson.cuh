@@ -4,18 +4,20 @@
 //   DG[s] = dg of column s              (the columns of dG^{k-m_k})
 //   W[s]  = du + beta D-hat dg          (the columns of dU + beta D-hat dG)
 // so the update u_AA = u - H g = u + beta D-hat g - (dU + beta D-hat dG) gamma
-// reads one ring.  The Gram matrix dG'dG is kept by slot and updated by one
-// row per iteration (the incremental update of Sec. 5); <dg_s, g^k> is carried
-// along as <dg_s, g^{k-1}> + <dg_s, dg_new>.
+// reads one ring.  The Gram matrix dG'dG is kept by slot; each entry is
+// formed once, at the first AA attempt after both of its columns exist (the
+// Gram pass below), and <dg_s, g^k> is summed at every attempt.
 //
-// Per iteration:
+// Per iteration (single LP):
 //   k_memory   (every iteration, Alg. 2 "for j = 1..m_k"): g^k = uh - u,
-//              dg = g^k - g^{k-1}, du = u^k - u^{k-1}; writes the new column;
-//              partial dot products <dg_s, dg> for the kept old columns,
-//              ||dg||^2, <dg, g^k>, ||du||^2.  Its last block updates the Gram
-//              matrix, the column list and, when the safeguard passed, solves
+//              dg = g^k - g^{k-1}, du = u^k - u^{k-1}; writes the new column
+//              and sums ||dg||^2, <dg, g^k>, ||du||^2; its last block appends
+//              the column to the list and, when the safeguard failed, ends
+//              the iteration (a PDHG step);
+//   k_gram     (safeguard passed): the pending Gram entries and the
+//              right-hand side in one pass over the columns, then the solve
 //              for gamma (Cholesky of dG'dG + eta I; or Reverse, AngleFilter,
-//              LengthFilter, Reverse and the QR solve of Alg. 3 from the Gram).
+//              LengthFilter, Reverse and the QR solve of Alg. 3 from the Gram);
 //   k_mix      (AA step accepted): u^{k+1} = P(u + beta D-hat g - W gamma),
 //              and du for the next column.  A PDHG step needs no pass: the
 //              roles of the two iterate components swap and du = g^k.
@@ -264,93 +266,9 @@ static __device__ void memory_solve_tail(DevState *st, const MethodParams &mp, i
     }
 }
 
-// The m x m work of one iteration for one LP, run by warp 0 of one block after
-// the memory pass's partial sums are reduced into red[]: the Gram row and
-// column of the new slot, the incremental right-hand side, the column list,
-// and, when the safeguard passed (st->want_aa), the solve of Alg. 2 or the
-// filters and solve of Alg. 3; then the counters and the next free slot.
-template <int MC>
-__device__ void memory_finalize(DevState *st, const MethodParams &mp, int M, const int *s_old,
-                                int nold, int sn, const double *red, SolveSmem &sm, const Trace &tr) {
-    const int lane = threadIdx.x & 31;
-    if (M > 0) {
-        // Gram row / column of the new slot; incremental right-hand side
-        // rhs_s(k) = rhs_s(k-1) + <dg_s, dg_new>; list = survivors + new column
-        for (int t = lane; t < nold; t += 32) {
-            const int s = s_old[t];
-            st->G[s * NSLOT + sn] = red[t];
-            st->G[sn * NSLOT + s] = red[t];
-            st->rhs[s] += red[t];
-            st->list[t] = s;
-        }
-        if (lane == 0) {
-            st->G[sn * NSLOT + sn] = red[MC];
-            st->rhs[sn] = red[MC + 1];
-            st->en2[sn] = red[MC + 2];
-            st->list[nold] = sn;
-            st->count = nold + 1;
-            st->new_slot = sn;
-        }
-        __syncwarp();
-    }
-    memory_solve_tail(st, mp, M, sm, tr);
-}
-
-// ---------------------------------------------------------------------------
-// Per-element work of the memory pass on W consecutive elements at e0.  The
-// old columns are read in groups of 8 with all loads of a group issued before
-// their use; the ring is read with evict-first loads (once per iteration).
-// ---------------------------------------------------------------------------
+// The ring's columns are read in groups of COLGRP with all loads of a group
+// issued before their use.
 constexpr int COLGRP = 8;
-
-// GN: also accumulate ||g^k||^2 into acc[MC + 3] (the batched path forms the
-// safeguard's residual norm here rather than in the half-steps).
-template <typename V, int MC, int W, bool GN = false>
-__device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int cur, bool prev_acc,
-                                             V beta, V *DGn, V *Wn, const int64_t *off, int nold,
-                                             Acc<V> (&acc)[MC + 3 + (GN ? 1 : 0)]) {
-    const V *UPs = reinterpret_cast<const V *>(P.UP);
-    const Pack<V, W> pa = ld<V, W>(UPs + 2 * e0), pb = ld<V, W>(UPs + 2 * e0 + W);
-    const Pack<V, W> gp = ld<V, W>(P.g + e0);
-    const Pack<V, W> dh = ld<V, W>(P.dh + e0);
-    Pack<V, W> wn;
-    if (prev_acc) wn = ld_stream<V, W>(Wn + e0);
-    Pack<V, W> gk, dgk, wk;
-    V dg[W];
-#pragma unroll
-    for (int i = 0; i < W; ++i) {
-        const int i0 = 2 * i, i1 = 2 * i + 1;
-        const V c0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
-        const V c1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
-        const V u = cur ? c1 : c0, uh = cur ? c0 : c1;
-        const V g = uh - u;
-        dg[i] = g - gp.v[i];
-        const V du = prev_acc ? wn.v[i] : gp.v[i];     // u^k - u^{k-1}
-        gk.v[i] = g;
-        dgk.v[i] = dg[i];
-        wk.v[i] = du + beta * dh.v[i] * dg[i];
-        acc[MC].add_sq(dg[i]);
-        acc[MC + 1].add_prod(dg[i], g);
-        acc[MC + 2].add_sq(du);
-        if constexpr (GN) acc[MC + 3].add_sq(g);
-    }
-    st<V, W>(P.g + e0, gk);
-    st<V, W>(DGn + e0, dgk);
-    st<V, W>(Wn + e0, wk);
-#pragma unroll
-    for (int s0 = 0; s0 < MC; s0 += COLGRP) {
-        if (s0 >= nold) break;
-        Pack<V, W> col[COLGRP];
-#pragma unroll
-        for (int j = 0; j < COLGRP; ++j)
-            if (s0 + j < MC && s0 + j < nold) col[j] = ld_stream<V, W>(P.DG + off[s0 + j] + e0);
-#pragma unroll
-        for (int j = 0; j < COLGRP; ++j)
-            if (s0 + j < MC && s0 + j < nold)
-#pragma unroll
-                for (int i = 0; i < W; ++i) acc[s0 + j].add_prod(col[j].v[i], dg[i]);
-    }
-}
 
 // ---------------------------------------------------------------------------
 // Single-LP memory pass, in two kernels.
@@ -370,17 +288,18 @@ __device__ __forceinline__ void memory_elems(const Prob<V> &P, int64_t e0, int c
 // other column t and the right-hand side <dg_t, g^k> of every column, then
 // solves (Alg. 2, or the filters of Alg. 3) in its last block.  Every Gram
 // entry is one dot product of two stored columns, formed once, as in the
-// incremental update of Sec. 5: with an attempt at every iteration k_gram
-// forms one row per iteration; with r failed safeguard tests in between it
-// forms the r rows in one pass instead of r passes, and none in iterations
-// without an attempt.
+// Gram update of Sec. 5 (one new row per column): with an attempt at every
+// iteration k_gram forms one row per iteration; with r failed safeguard
+// tests in between it forms the r rows in one pass instead of r passes, and
+// none in iterations without an attempt.
 // ---------------------------------------------------------------------------
 
 // Per-element work of k_memory on W consecutive elements at e0:
-// acc[0] ||dg||^2, acc[1] <dg, g^k>, acc[2] ||du||^2.
-template <typename V, int W>
+// acc[0] ||dg||^2, acc[1] <dg, g^k>, acc[2] ||du||^2; GN: acc[3] ||g^k||^2
+// (the batched path forms the safeguard's residual norm here).
+template <typename V, int W, bool GN = false>
 __device__ __forceinline__ void push_elems(const Prob<V> &P, int64_t e0, int cur, bool prev_acc,
-                                           V beta, V *DGn, V *Wn, Acc<V> (&acc)[3]) {
+                                           V beta, V *DGn, V *Wn, Acc<V> (&acc)[GN ? 4 : 3]) {
     const V *UPs = reinterpret_cast<const V *>(P.UP);
     const Pack<V, W> pa = ld_stream<V, W>(UPs + 2 * e0), pb = ld_stream<V, W>(UPs + 2 * e0 + W);
     const Pack<V, W> gp = ld_stream<V, W>(P.g + e0);
@@ -403,6 +322,7 @@ __device__ __forceinline__ void push_elems(const Prob<V> &P, int64_t e0, int cur
         acc[0].add_sq(dg);
         acc[1].add_prod(dg, g);
         acc[2].add_sq(du);
+        if constexpr (GN) acc[3].add_sq(g);
     }
     st<V, W>(P.g + e0, gk);
     st<V, W>(DGn + e0, dgk);
@@ -431,7 +351,6 @@ static __device__ void push_finalize(DevState *st, const MethodParams &mp, int M
     }
     __syncwarp();
     if (M > 0 && st->want_aa) return;                   // k_gram finishes the iteration
-    if (lane == 0) st->rhs_fresh = 0;                   // rhs lags g^k from here on
     memory_solve_tail(st, mp, M, sm, tr);
 }
 
@@ -472,7 +391,6 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
         if (threadIdx.x == 0) {
             st->count = 0;
             st->stale = 0ull;
-            st->rhs_fresh = 0;
             st->want_aa = 0;  // a restart takes the plain step
             st->new_slot = 0;
             st->free_slot = 0;
@@ -617,6 +535,53 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// The Gram pass's work list for one LP with k columns list[0..k) (oldest
+// first), `stale` the slots whose entries with the other columns are pending:
+// every pair (a, b), a < b < k, of list positions with a stale column, then
+// the pairs (a, k), a < k - 1, of a column with g^k (position k).  The
+// right-hand side <dg_s, g^k> is always summed directly: carried as
+// <dg_s, g^{k-1}> + <dg_s, dg> (the update of Sec. 5) it loses its relative
+// accuracy to cancellation once g^k is much smaller than g^{k-1}.  The newest
+// column's <dg, g^k> comes from the memory pass.  Returns the pair count.
+// One thread.
+static __device__ int gram_pair_list(const int *list, int k, uint64_t stale, int16_t *pa, int16_t *pb) {
+    int np = 0;
+    for (int a = 0; a < k; ++a)
+        for (int b = a + 1; b < k; ++b)
+            if (((stale >> list[a]) | (stale >> list[b])) & 1ull) {
+                pa[np] = (int16_t)a;
+                pb[np] = (int16_t)b;
+                ++np;
+            }
+    for (int a = 0; a + 1 < k; ++a) {
+        pa[np] = (int16_t)a;
+        pb[np] = (int16_t)k;
+        ++np;
+    }
+    return np;
+}
+
+// Gram entries and right-hand side from the pair values v[0..np) of
+// gram_pair_list, then the stale set cleared.  One warp (lanes stride the
+// pairs).
+static __device__ void gram_store(DevState *st, const int *list, int k, const int16_t *pa,
+                                  const int16_t *pb, int np, const double *v) {
+    const int lane = threadIdx.x & 31;
+    for (int p = lane; p < np; p += 32) {
+        const int a = list[pa[p]], bv = pb[p];
+        if (bv == k) {
+            st->rhs[a] = v[p];
+        } else {
+            const int b = list[bv];
+            st->G[a * NSLOT + b] = v[p];
+            st->G[b * NSLOT + a] = v[p];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) st->stale = 0ull;
+    __syncwarp();
+}
+
 template <typename V>
 __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
     constexpr int W = 16 / sizeof(V);
@@ -626,7 +591,7 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
     if (st->done | st->error) return;
     if (!st->want_aa || mp.method == 0 || mp.mem == 0) return;
     extern __shared__ __align__(128) unsigned char gram_smem[];
-    __shared__ int s_k, s_np, s_fail, s_incr;
+    __shared__ int s_k, s_np, s_fail;
     __shared__ int s_list[NSLOT];
     __shared__ uint64_t s_stale;
     __shared__ int16_t s_pa[GRAM_MAXPAIRS], s_pb[GRAM_MAXPAIRS];
@@ -641,30 +606,7 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
     if (threadIdx.x < NSLOT) s_list[threadIdx.x] = st->list[threadIdx.x];
     __syncthreads();
     if (threadIdx.x == 0) {                              // the pair list, from shared memory
-        const int k = s_k;
-        const uint64_t stale = s_stale;
-        // The last iteration was an attempt and only the newest column is
-        // stale: its row gives the right-hand side incrementally,
-        // <dg_s, g^k> = <dg_s, g^{k-1}> + <dg_s, dg> (the update of Sec. 5),
-        // so the row is the only pass needed.  Otherwise every column's
-        // <dg_s, g^k> is summed directly.
-        const int incr = st->rhs_fresh && k >= 2 && stale == (1ull << s_list[k - 1]);
-        int np = 0;
-        for (int a = 0; a < k; ++a)
-            for (int b = a + 1; b < k; ++b)
-                if (((stale >> s_list[a]) | (stale >> s_list[b])) & 1ull) {
-                    s_pa[np] = (int16_t)a;
-                    s_pb[np] = (int16_t)b;
-                    ++np;
-                }
-        if (!incr)
-            for (int a = 0; a + 1 < k; ++a) {          // the newest column's <dg, g^k> is known
-                s_pa[np] = (int16_t)a;
-                s_pb[np] = (int16_t)k;
-                ++np;
-            }
-        s_np = np;
-        s_incr = incr;
+        s_np = gram_pair_list(s_list, s_k, s_stale, s_pa, s_pb);
         for (int s2 = 0; s2 < GRAM_STAGES; ++s2) {
             mbar_init(&full[s2], 1);
             mbar_init(&empty[s2], GRAM_CWARPS);
@@ -776,16 +718,12 @@ __global__ void __launch_bounds__(BLOCK) k_gram(Prob<V> P, MethodParams mp) {
                 const int b = s_list[bv];
                 st->G[a * NSLOT + b] = v;
                 st->G[b * NSLOT + a] = v;
-                if (s_incr) st->rhs[a] += v;            // (b is the newest column)
             }
         }
     }
     __syncthreads();
     if (threadIdx.x >= 32) return;
-    if (lane == 0) {
-        st->stale = 0ull;
-        st->rhs_fresh = 1;
-    }
+    if (lane == 0) st->stale = 0ull;
     __syncwarp();
     memory_solve_tail(st, mp, mp.mem, sm, P.tr);
 }

@@ -309,7 +309,10 @@ template <typename V> aapdhg_status bensure_rings(bh_t h) {
     if (h->have_rings) return AAPDHG_OK;
     P.DG = (V *)bdev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
     P.W = (V *)bdev_alloc(h, sizeof(V) * (size_t)NSLOT * h->Npad);
-    if (!P.DG || !P.W) return bfail(h, AAPDHG_ERR_OOM, "device allocation of the Anderson memory failed");
+    BatchView<V> &B = bview<V>(h);
+    B.gpart = (double *)bdev_alloc(h, sizeof(double) * (size_t)GRAM_MAXPAIRS * B.nchunk);
+    if (!P.DG || !P.W || !B.gpart)
+        return bfail(h, AAPDHG_ERR_OOM, "device allocation of the Anderson memory failed");
     h->have_rings = true;
     return AAPDHG_OK;
 }
@@ -398,11 +401,17 @@ template <typename V, int MC> void blaunch_memory_mix(bh_t h, int cur) {
     Prob<V> &P = bprob<V>(h);
     BatchView<V> &B = bview<V>(h);
     const int M = (h->mp.method == 0) ? 0 : h->mp.mem;
+    const int fp64 = h->prec == AAPDHG_FP64 ? 1 : 0;
     bmark_begin(h, BK_MEMORY);
-    k_memory_b<V, MC><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
+    k_memory_b<V><<<B.nchunk, BLOCK, 0, h->stream>>>(P, B, h->mp, cur);
     bmark_end(h);
-    bmark_begin(h, BK_GRAM);
-    k_gram_b<MC><<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, h->prec == AAPDHG_FP64 ? 1 : 0, h->mp);
+    bmark_begin(h, BK_GRAM);             // the push, and the Gram pass of the attempts
+    k_gram_b<<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, fp64, h->mp);
+    if (M > 0) {
+        k_gram_cols_b<V><<<dim3(B.nchunk, M), BLOCK, 0, h->stream>>>(P, B);
+        k_solve_b<<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, fp64, h->mp);
+        h->launches += 2;
+    }
     bmark_end(h);
     if (M > 0) {
         bmark_begin(h, BK_MIX);
@@ -514,7 +523,7 @@ template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
 int launches_per_iter(bh_t h, int64_t g) {
     const bool kkt = h->kkt_every > 0 && g >= 1 && (g - 1) % h->kkt_every == 0;
     const bool mix = h->mp.method != 0 && h->mp.mem > 0;
-    return 4 + (kkt ? 1 : 0) + (mix ? 1 : 0);
+    return 4 + (kkt ? 1 : 0) + (mix ? 3 : 0);
 }
 
 template <typename V> bool blaunch_chunk_graph(bh_t h, int64_t g0) {

@@ -24,10 +24,14 @@
 //                          on KKT iterations the KKT terms of u^k per element;
 //   k_kkt_b                per-problem KKT of u^k (Remark on termination) and
 //                          the stop test (KKT iterations only);
-//   k_memory_b             per chunk of a problem's elements: the memory pass
-//                          plus ||g^k||^2 (chunk partial sums);
+//   k_memory_b             per chunk of a problem's elements: the new memory
+//                          column plus ||g^k||^2 (chunk partial sums);
 //   k_gram_b               per problem (one warp): the fixed-order reduction of
-//                          its chunk partials, its safeguard and m x m work;
+//                          its chunk partials, its safeguard, the column
+//                          appended (and, when the safeguard failed, the end
+//                          of its iteration);
+//   k_gram_cols_b, k_solve_b  the Gram pass and the m x m work of the problems
+//                          whose safeguard passed (their AA attempts);
 //   k_mix_b                the AA mix of the problems whose step was accepted.
 #pragma once
 #include "anderson.cuh"
@@ -37,7 +41,7 @@
 namespace aap {
 
 constexpr int BCHUNK = 8192;          // elements per chunk of a problem (multiple of 4)
-constexpr int NBV = MAXM + 4;         // chunk partial columns: Gram row, ||dg||^2, <dg,g>, ||du||^2, ||g||^2
+constexpr int NBV = 5;                // chunk partial columns (the KKT terms; the memory pass uses 4)
 
 template <typename V> struct BatchView {
     int32_t nprob;
@@ -50,6 +54,7 @@ template <typename V> struct BatchView {
     const int4 *chunk;                // chunk -> (problem, first element, length, 0: x part / 1: y part)
     const int32_t *pchunk0;           // problem -> first chunk (nprob + 1 entries)
     double *cpart;                    // nchunk * NBV chunk partials
+    double *gpart;                    // nchunk * GRAM_MAXPAIRS Gram-pass partials (with a memory)
     uint32_t *pcnt;                   // per-problem arrival counters (self-resetting)
     const double *pnorm;              // per problem: ||q||, ||c|| of the caller's LP
     const double *ptol;               // per-problem tolerances, or null (one tolerance for all)
@@ -248,12 +253,14 @@ __global__ void __launch_bounds__(BLOCK) k_kkt_b(BatchView<V> B, double tol, int
 
 // --------------------------------------------------------------------------
 // Memory pass and ||g^k||^2, per chunk (one block each): a pure stream that
-// writes the chunk's partial sums.  A problem that stopped at this
-// iteration's KKT test (done == 1) has its iterate copied into both
-// components instead.  The per-problem reduction and m x m work follow in
-// k_gram_b, so no block holds its SM slot through a solve.
+// writes the new memory column of the chunk's problem (dg, and du + beta
+// D-hat dg) and the chunk's partial sums ||dg||^2, <dg, g^k>, ||du||^2 and
+// ||g^k||^2 (columns 0-3 of cpart).  No old column is read: the new column's
+// Gram entries are formed at the problem's next AA attempt (k_gram_cols_b),
+// as in the single-LP solver.  A problem that stopped at this iteration's KKT
+// test (done == 1) has its iterate copied into both components instead.
 // --------------------------------------------------------------------------
-template <typename V, int MC>
+template <typename V>
 __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, MethodParams mp, int cur) {
     constexpr int W = 16 / sizeof(V);
     typedef typename Vec2<V>::T V2;
@@ -277,28 +284,9 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
     const int M = (mp.method == 0) ? 0 : mp.mem;
     if (M == 0 && !B.pw_on) return;
     const bool fresh = init || restart || M == 0;   // only g^k and ||g^k||^2
-    __shared__ int64_t s_off[NSLOT];
-    __shared__ int s_nold, s_new, s_prev_acc;
-    __shared__ typename Acc<V>::Packed sh[WARPS * (MC + 4)];
-    if (threadIdx.x == 0) {
-        const int cnt = fresh ? 0 : st->count;
-        const int drop = (cnt == M) ? 1 : 0;
-        s_nold = cnt - drop;
-        s_new = fresh ? 0 : st->free_slot;
-        s_prev_acc = fresh ? 0 : st->accept;
-    }
-    __syncthreads();
-    if (threadIdx.x < NSLOT) {
-        const int t = threadIdx.x;
-        const int drop = (!fresh && st->count == M) ? 1 : 0;
-        s_off[t] = (int64_t)(t < s_nold ? st->list[t + drop] : 0) * P.Npad;
-    }
-    __syncthreads();
-    const int nold = s_nold, sn = s_new;
-    const bool prev_acc = s_prev_acc != 0;
-
-    // [0, nold): <dg_s, dg>; MC: ||dg||^2; MC+1: <dg, g>; MC+2: ||du||^2; MC+3: ||g||^2
-    Acc<V> acc[MC + 4];
+    __shared__ typename Acc<V>::Packed sh[WARPS * 4];
+    // 0 ||dg||^2, 1 <dg, g>, 2 ||du||^2, 3 ||g||^2
+    Acc<V> acc[4];
     const int64_t stride = (int64_t)BLOCK * W;
     if (fresh) {
         // g^k = T u^k - u^k (at the start: g^0 = u^1 - u^0, u^1 = T u^0 just
@@ -313,41 +301,40 @@ __global__ void __launch_bounds__(BLOCK) k_memory_b(Prob<V> P, BatchView<V> B, M
                 const V a0 = i0 < W ? pa.v[i0 % W] : pb.v[i0 % W];
                 const V a1 = i1 < W ? pa.v[i1 % W] : pb.v[i1 % W];
                 gk.v[i] = (cur ? a0 : a1) - (cur ? a1 : a0);
-                acc[MC + 3].add_sq(gk.v[i]);
+                acc[3].add_sq(gk.v[i]);
             }
             aap::st<V, W>(P.g + e, gk);
         }
     } else {
+        const int sn = st->free_slot;
+        const bool prev_acc = st->accept != 0;
         V *DGn = P.DG + (int64_t)sn * P.Npad;
         V *Wn = P.W + (int64_t)sn * P.Npad;
         const V beta = (V)mp.beta;
         for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += stride)
-            memory_elems<V, MC, W, true>(P, e, cur, prev_acc, beta, DGn, Wn, s_off, nold, acc);
+            push_elems<V, W, true>(P, e, cur, prev_acc, beta, DGn, Wn, acc);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < MC + 4; ++k) {
-        if (k < nold || k >= MC) {
-            acc[k].warp_allreduce();
-            if (lane == 0) sh[warp * (MC + 4) + k] = acc[k].pack();
-        }
+    for (int k = 0; k < 4; ++k) {
+        acc[k].warp_allreduce();
+        if (lane == 0) sh[warp * 4 + k] = acc[k].pack();
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < MC + 4; k += BLOCK) {
-        if (k < nold || k >= MC) {
-            double v = 0.0;
-            for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * (MC + 4) + k]);
-            B.cpart[(int64_t)blockIdx.x * NBV + (k < MC ? k : MAXM + (k - MC))] = v;
-        }
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * 4 + threadIdx.x]);
+        B.cpart[(int64_t)blockIdx.x * NBV + threadIdx.x] = v;
     }
 }
 
 // --------------------------------------------------------------------------
 // Per-problem reduction of the memory pass's chunk partials (fixed order),
-// the safeguard of Alg. 2 / Alg. 3 and the m x m work (the single-LP code).
-// Grid: one warp per problem.
+// the safeguard of Alg. 2 / Alg. 3, and the new column appended to the
+// problem's memory (the single-LP push).  A problem whose safeguard failed
+// ends its iteration here (a PDHG step); one whose safeguard passed is
+// finished by k_gram_cols_b and k_solve_b.  Grid: one warp per problem.
 // --------------------------------------------------------------------------
-template <int MC>
 __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<double> Bd, int fp64,
                                                MethodParams mp) {
     const int p = blockIdx.x;
@@ -360,6 +347,7 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
         if (lane == 0) {
             st->done = 2;
             st->restart = 0;              // an update at the stop iteration is not applied
+            st->want_aa = 0;
         }
         return;
     }
@@ -367,65 +355,48 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     const bool restart = !init && st->restart;       // primal weight update (R15)
     const int M = (mp.method == 0) ? 0 : mp.mem;
     const bool norm = M > 0 || (fp64 ? Bd.pw_on : Bf.pw_on);
-    __shared__ int s_old[NSLOT];
-    __shared__ double red[MC + 3];
-    __shared__ double gsq;
+    __shared__ double red[4];
     __shared__ SolveSmem sm;
-    const int cnt = (init || restart) ? 0 : st->count;
-    const int drop = (M > 0 && cnt == M) ? 1 : 0;
-    const int nold = cnt - drop;
-    const int sn = init ? 0 : st->free_slot;
-    for (int t = lane; t < nold; t += 32) s_old[t] = st->list[t + drop];
-    // fixed-order sums over the problem's chunks: Gram row, ||dg||^2, <dg,g>,
-    // ||du||^2, ||g||^2
+    // lane k sums column k over the problem's chunks in chunk order: one
+    // FP64 add per chunk and lane, no cross-lane tree (FP64 issue is the
+    // scarce resource here)
     const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
-    if (norm) {
-        // lane k sums column k over the problem's chunks in chunk order: one
-        // FP64 add per chunk and lane, no cross-lane tree (FP64 issue is the
-        // scarce resource here)
-        for (int k = lane; k < MC + 4; k += 32) {
-            if (!(k < nold || k >= MC)) continue;
-            const int col = k < MC ? k : MAXM + (k - MC);
-            double v = 0.0;
-            for (int c = c0; c < c1; ++c) v += __ldcg(cpart + (int64_t)c * NBV + col);
-            if (k < MC + 3) red[k] = v;
-            else gsq = v;
-        }
+    const bool fresh = init || restart || M == 0;
+    if (norm && lane < 4 && (!fresh || lane == 3)) {
+        double v = 0.0;
+        for (int c = c0; c < c1; ++c) v += __ldcg(cpart + (int64_t)c * NBV + lane);
+        red[lane] = v;
     }
     __syncwarp();
-    const double gn = norm ? sqrt(gsq) : 0.0;
-    if (init) {
+    const double gn = norm ? sqrt(red[3]) : 0.0;
+    if (init || restart) {
         if (lane == 0) {
             if (!isfinite(gn)) st->error = 1;
-            st->g0 = gn;
+            st->gnorm_prev = init ? NAN : st->gnorm;
             st->gnorm = gn;
-            st->gnorm_prev = NAN;
+            if (init) st->g0 = gn;
             st->count = 0;
+            st->stale = 0ull;
+            st->want_aa = 0;
             st->new_slot = 0;
             st->free_slot = 0;
-            st->accept = 0;   // u^1 = T u^0 behaves as a PDHG step: du^0 = g^0
+            st->accept = 0;   // u^1 = T u^0 (or the restart step) behaves as a PDHG step
             st->use_count = 0;
-            st->it = 0;
-            st->init_done = 1;
+            if (init) {
+                st->it = 0;
+                st->init_done = 1;
+            } else {
+                st->n_pd += 1;
+                st->restart = 0;
+                st->it += 1;
+            }
         }
         return;
     }
     if (!isfinite(gn)) {
-        if (lane == 0) st->error = 1;
-        return;
-    }
-    if (restart) {                        // a plain step; the memory restarts from it
         if (lane == 0) {
-            st->gnorm_prev = st->gnorm;
-            st->gnorm = gn;
-            st->count = 0;
-            st->new_slot = 0;
-            st->free_slot = 0;
-            st->accept = 0;
-            st->use_count = 0;
-            st->n_pd += 1;
-            st->restart = 0;
-            st->it += 1;
+            st->error = 1;
+            st->want_aa = 0;
         }
         return;
     }
@@ -439,7 +410,127 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     }
     __syncwarp();
     const Trace none{0, nullptr, nullptr, nullptr, nullptr};
-    memory_finalize<MC>(st, mp, M, s_old, nold, sn, red, sm, none);
+    push_finalize(st, mp, M, M > 0 ? st->free_slot : 0, red, sm, none);
+}
+
+// --------------------------------------------------------------------------
+// The Gram pass of the problems whose safeguard passed, in two kernels (the
+// single-LP k_gram's work, per problem):
+//   k_gram_cols_b  one block per (chunk, list position a) of such a problem:
+//                  the chunk's partial dot products of column a with its
+//                  partners in gram_pair_list (the columns b > a of its pairs
+//                  (a, b), then g^k for the right-hand side), into gpart at
+//                  the pairs' list indices;
+//   k_solve_b      per such problem (one warp): the pairs' sums over its
+//                  chunks in chunk order, the Gram entries and right-hand
+//                  side, then the solve of Alg. 2 or the filters and solve of
+//                  Alg. 3 and the end of the iteration.
+// The blocks of one chunk read its column a once each and the partners
+// (mostly the newest column and g^k) through L2, so an attempt moves about
+// the k + 1 vectors once.  A block takes its partners GRAM_PG at a time.
+// Every sum depends on the problem's own data only.
+// --------------------------------------------------------------------------
+constexpr int GRAM_PG = 8;                      // partners per pass over the chunk
+
+template <typename V>
+__global__ void __launch_bounds__(BLOCK) k_gram_cols_b(Prob<V> P, BatchView<V> B) {
+    constexpr int W = 16 / sizeof(V);
+    const int4 ch = B.chunk[blockIdx.x];
+    const DevState *st = B.stb + ch.x;
+    if (stopped(st) || !st->init_done || !st->want_aa) return;
+    const int a = blockIdx.y, k = st->count;
+    if (a >= k) return;
+    __shared__ int s_pidx[NSLOT];                  // list index of each partner's pair
+    __shared__ const V *s_vec[NSLOT];              // partner vectors
+    __shared__ const V *s_col;
+    __shared__ int s_np;
+    __shared__ typename Acc<V>::Packed sh[WARPS * GRAM_PG];
+    if (threadIdx.x == 0) {
+        int list[NSLOT];
+        for (int t = 0; t < k; ++t) list[t] = st->list[t];
+        const uint64_t stale = st->stale;
+        // the pairs of gram_pair_list in its order: (a', b) row pairs, then (a', k)
+        int idx = 0, np = 0;
+        for (int a2 = 0; a2 < k; ++a2)
+            for (int b = a2 + 1; b < k; ++b)
+                if (((stale >> list[a2]) | (stale >> list[b])) & 1ull) {
+                    if (a2 == a) {
+                        s_pidx[np] = idx;
+                        s_vec[np] = P.DG + (int64_t)list[b] * P.Npad;
+                        ++np;
+                    }
+                    ++idx;
+                }
+        if (a + 1 < k) {
+            s_pidx[np] = idx + a;
+            s_vec[np] = P.g;
+            ++np;
+        }
+        s_np = np;
+        s_col = P.DG + (int64_t)list[a] * P.Npad;
+    }
+    __syncthreads();
+    const int np = s_np;
+    const V *col = s_col;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t e0 = ch.y, e1 = (int64_t)ch.y + ch.z;
+    for (int j0 = 0; j0 < np; j0 += GRAM_PG) {
+        Acc<V> acc[GRAM_PG];
+        for (int64_t e = e0 + (int64_t)threadIdx.x * W; e < e1; e += (int64_t)BLOCK * W) {
+            const Pack<V, W> x = ld<V, W>(col + e);
+#pragma unroll
+            for (int j = 0; j < GRAM_PG; ++j)
+                if (j0 + j < np) {
+                    const Pack<V, W> y = ld<V, W>(s_vec[j0 + j] + e);
+#pragma unroll
+                    for (int i = 0; i < W; ++i) acc[j].add_prod(x.v[i], y.v[i]);
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < GRAM_PG; ++j) {
+            acc[j].warp_allreduce();
+            if (lane == 0) sh[warp * GRAM_PG + j] = acc[j].pack();
+        }
+        __syncthreads();
+        if (threadIdx.x < GRAM_PG && j0 + threadIdx.x < np) {
+            double v = 0.0;
+            for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * GRAM_PG + threadIdx.x]);
+            B.gpart[(int64_t)blockIdx.x * GRAM_MAXPAIRS + s_pidx[j0 + threadIdx.x]] = v;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(32) k_solve_b(BatchView<float> Bf, BatchView<double> Bd, int fp64,
+                                                MethodParams mp) {
+    const int p = blockIdx.x;
+    DevState *st = fp64 ? Bd.stb + p : Bf.stb + p;
+    if (stopped(st) || !st->init_done || !st->want_aa) return;
+    const int32_t *pchunk0 = fp64 ? Bd.pchunk0 : Bf.pchunk0;
+    const double *gpart = fp64 ? Bd.gpart : Bf.gpart;
+    const int lane = threadIdx.x;
+    __shared__ int s_list[NSLOT];
+    __shared__ int16_t s_pa[GRAM_MAXPAIRS], s_pb[GRAM_MAXPAIRS];
+    __shared__ double s_val[GRAM_MAXPAIRS];
+    __shared__ int s_np;
+    __shared__ SolveSmem sm;
+    const int k = st->count;
+    if (lane == 0) {
+        for (int a = 0; a < k; ++a) s_list[a] = st->list[a];
+        s_np = gram_pair_list(s_list, k, st->stale, s_pa, s_pb);
+    }
+    __syncwarp();
+    const int np = s_np;
+    const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
+    for (int pr = lane; pr < np; pr += 32) {           // chunk order
+        double v = 0.0;
+        for (int c = c0; c < c1; ++c) v += __ldcg(gpart + (int64_t)c * GRAM_MAXPAIRS + pr);
+        s_val[pr] = v;
+    }
+    __syncwarp();
+    gram_store(st, s_list, k, s_pa, s_pb, np, s_val);
+    const Trace none{0, nullptr, nullptr, nullptr, nullptr};
+    memory_solve_tail(st, mp, mp.mem, sm, none);
 }
 
 // --------------------------------------------------------------------------

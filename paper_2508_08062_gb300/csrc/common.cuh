@@ -132,7 +132,6 @@ struct DevState {
     uint32_t cnt_norm;     // last-block counter of the norm kernels
     uint64_t stale;        // single LP: slots whose Gram entries with the other columns are pending
     uint32_t cnt_gram;     // last-block counter of the Gram pass
-    int32_t rhs_fresh;     // single LP: the last iteration was an AA attempt, so rhs[s] = <dg_s, g^{k-1}>
     double scratch[8];     // (kept by a reset: ||q||^2, ||c||^2 of the create)
 };
 

@@ -354,8 +354,11 @@ PW_CASES = {
 }
 # Member 4 (5 x 9) amplifies 1e-15 perturbations of the steps to ~1.5e-9 over
 # these 160 iterations under AA / FAA with the update (oracle against itself),
-# so its iterates are not compared at 1e-9 there.
-PW_CHECKED = {"aa5": (0, 1, 2, 3, 5), "faa6": (0, 1, 2, 3, 5), "aa5_theta1_noblend": (0, 1, 2, 3, 5)}
+# so its iterates are not compared at 1e-9 there.  Member 5 (the box LP) under
+# AA m = 5 turns a 1e-15 relative change of tau into 3.0e-9 at k = 27 (oracle
+# against itself), so its iterates are held to 1e-8 there.
+PW_CHECKED = {"aa5": (0, 1, 2, 3), "faa6": (0, 1, 2, 3, 5), "aa5_theta1_noblend": (0, 1, 2, 3)}
+PW_LOOSE = {"aa5": {5: 1e-8}, "aa5_theta1_noblend": {5: 1e-8}}
 
 
 def _pw_steps(probs):
@@ -369,6 +372,7 @@ def test_fp64_batch_primal_weight_iterates_match_oracle(name):
     iters, period = 160, 40
     probs = _members() + [_box()]
     checked = PW_CHECKED.get(name, range(len(probs)))
+    loose = PW_LOOSE.get(name, {})
     taus, sigs = _pw_steps(probs)
     kw = PW_CASES[name]
     refs = [O.solve(O.OracleLP.from_problem(P), O.Params(tau=t, sigma=s, pw_period=period, **kw), iters,
@@ -383,9 +387,9 @@ def test_fp64_batch_primal_weight_iterates_match_oracle(name):
         for k in range(iters + 1):
             got = b.get_iterate()
             for p, (x, y) in enumerate(got):
-                if p in checked:
+                if p in checked or p in loose:
                     err = _rel(np.concatenate([x, y]), refs[p].rec_u[k])
-                    assert err <= FP64_TOL, (name, p, k, err)
+                    assert err <= loose.get(p, FP64_TOL), (name, p, k, err)
             if k < iters:
                 b.iterate(1)
         st = b.status()

@@ -211,6 +211,26 @@ aapdhg_status aapdhg_get_trace(aapdhg_t h, int64_t *len, int8_t *branch, double 
 aapdhg_status aapdhg_get_memory(aapdhg_t h, int32_t capacity, int32_t *count, double *gram,
                                 double *rhs, double *dg, double *g);
 
+/* Checkpoint / resume of a run (the paper has none; its experiments stop at a
+ * time limit).  aapdhg_state_size gives the bytes of the handle's state blob;
+ * aapdhg_get_state copies the blob into the caller's host buffer `buf` of
+ * exactly that size: the run state on the device (the iterates u^k and
+ * T(u^k) as pairs, g^k, D-hat, the two Anderson rings with the Gram matrix,
+ * column list, counters i^k, j^k and the safeguard's g^0, the primal-weight
+ * snapshot) and on the host (the step sizes and primal weight, the layouts,
+ * the time used).  aapdhg_set_state restores a blob into a handle created
+ * from the same LP in the same precision with the same set-up calls
+ * (scaling, method and memory, primal weight period); it rebuilds the layouts
+ * when they differ, so that every sum runs in the blob's order.  Iterating
+ * after a restore gives bit for bit what the run the blob was taken from
+ * gives.  The caller owns the buffer; nothing is kept.  A NULL buffer, a size
+ * other than aapdhg_state_size (get) or the blob's own (set), a blob of
+ * another LP, precision or set-up, or a corrupt header gives
+ * AAPDHG_ERR_INVALID.                                                         */
+aapdhg_status aapdhg_state_size(aapdhg_t h, size_t *bytes);
+aapdhg_status aapdhg_get_state(aapdhg_t h, void *buf, size_t bytes);
+aapdhg_status aapdhg_set_state(aapdhg_t h, const void *buf, size_t bytes);
+
 /* Kernel instrumentation for benchmarks.  aapdhg_profile_kernels(h, 1) makes
  * aapdhg_iterate bracket every kernel it launches with CUDA events recorded on
  * the handle's stream and accumulate the elapsed times per kernel kind; it

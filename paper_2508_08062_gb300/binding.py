@@ -32,7 +32,8 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_set_method", "aapdhg_set_scaling", "aapdhg_set_start", "aapdhg_reset",
            "aapdhg_iterate", "aapdhg_set_time_limit",
            "aapdhg_get_iterate", "aapdhg_get_kkt", "aapdhg_get_counters", "aapdhg_set_trace",
-           "aapdhg_get_trace", "aapdhg_get_memory", "aapdhg_profile_kernels",
+           "aapdhg_get_trace", "aapdhg_get_memory", "aapdhg_state_size", "aapdhg_get_state",
+           "aapdhg_set_state", "aapdhg_profile_kernels",
            "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
            "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_set_layout",
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
     L.aapdhg_set_trace.argtypes = [vp, i64]
     L.aapdhg_get_trace.argtypes = [vp, C.POINTER(i64), vp, vp, vp, vp]
     L.aapdhg_get_memory.argtypes = [vp, i32, vp, vp, vp, vp, vp]
+    L.aapdhg_state_size.argtypes = [vp, C.POINTER(C.c_size_t)]
+    L.aapdhg_get_state.argtypes = [vp, vp, C.c_size_t]
+    L.aapdhg_set_state.argtypes = [vp, vp, C.c_size_t]
     L.aapdhg_profile_kernels.argtypes = [vp, i32]
     L.aapdhg_get_kernel_profile.argtypes = [vp, i32, C.POINTER(i64), C.POINTER(f64)]
     L.aapdhg_kkt_noalloc.argtypes = [i32, i32] + [vp] * 15
@@ -359,6 +363,19 @@ class Solver:
                                                _ptr(rhs), _ptr(dg), _ptr(g)))
         k = cnt.value
         return dict(count=k, gram=gram[:k * k].reshape(k, k), rhs=rhs[:k], dg=dg[:k], g=g)
+
+    def get_state(self):
+        """The run's state blob (bytes): restoring it with set_state, here or in a
+        handle made from the same LP with the same set-up, resumes the run exactly."""
+        n = C.c_size_t()
+        self._check(self._L.aapdhg_state_size(self._h, C.byref(n)))
+        buf = np.zeros(n.value, dtype=np.uint8)
+        self._check(self._L.aapdhg_get_state(self._h, _ptr(buf), n))
+        return buf.tobytes()
+
+    def set_state(self, blob):
+        buf = np.frombuffer(bytes(blob), dtype=np.uint8).copy()
+        self._check(self._L.aapdhg_set_state(self._h, _ptr(buf), C.c_size_t(buf.size)))
 
     LAYOUT_CANDIDATES = ((32, 1024), (16, 1024), (64, 1024), (128, 1024), (32, 2048), (64, 2048),
                          (128, 2048), (64, 4096))

@@ -1306,6 +1306,141 @@ template <typename V> aapdhg_status set_scaling_t(aapdhg_t h, int32_t ruiz_iters
 // ===========================================================================
 // C ABI
 // ===========================================================================
+// ---------------------------------------------------------------------------
+// Checkpoint / resume.  A state blob is a header (the LP's sizes and set-up,
+// which must match the handle it is restored into, and the host-side run
+// state: steps, primal-weight state, layouts, time used) followed by the
+// device arrays in a fixed order: DevState, the iterate pairs, g, D-hat, then
+// (when allocated) the two rings and the primal-weight snapshot and base
+// D-hat.  Restoring it and iterating gives bit for bit what the run it was
+// taken from gives.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint64_t STATE_MAGIC = 0x31545354'47445041ull;   // "APDGTST1"
+
+struct StateHeader {
+    uint64_t magic;
+    int32_t prec, m, n, method, mem, scaled, rings, pw_snap, pw_base, dhat_mode, pad;
+    int64_t nnz, N, Npad, pw_period, pw_last_k, bytes;
+    LayoutParams lay[2];
+    MethodParams mp;
+    double pw_gamma, pw_omega, pw_best_kkt, tau_user, sigma_user, time_used;
+};
+
+size_t state_bytes(aapdhg_t h) {
+    const size_t sv = h->prec == AAPDHG_FP64 ? 8 : 4;
+    const bool rings = (h->prec == AAPDHG_FP64 ? (void *)h->pd.DG : (void *)h->pf.DG) != nullptr;
+    size_t b = sizeof(StateHeader) + sizeof(DevState) + sv * (size_t)h->N * 4;   // pairs, g, D-hat
+    if (rings) b += 2 * sv * (size_t)NSLOT * h->Npad;
+    if (h->pw_snap) b += sv * (size_t)h->N;
+    if (h->pw_dh_base && h->pw_base_valid) b += sv * (size_t)h->N;
+    return b;
+}
+
+// The device arrays of the blob, in order: (device pointer, bytes).
+template <typename V> std::vector<std::pair<void *, size_t>> state_arrays(aapdhg_t h, bool rings, bool snap,
+                                                                            bool base) {
+    Prob<V> &P = prob<V>(h);
+    const size_t N = (size_t)h->N;
+    std::vector<std::pair<void *, size_t>> a;
+    a.push_back({h->st, sizeof(DevState)});
+    a.push_back({P.UP, sizeof(typename Vec2<V>::T) * N});
+    a.push_back({P.g, sizeof(V) * N});
+    a.push_back({const_cast<V *>(P.dh), sizeof(V) * N});
+    if (rings) {
+        a.push_back({P.DG, sizeof(V) * (size_t)NSLOT * h->Npad});
+        a.push_back({P.W, sizeof(V) * (size_t)NSLOT * h->Npad});
+    }
+    if (snap) a.push_back({h->pw_snap, sizeof(V) * N});
+    if (base) a.push_back({h->pw_dh_base, sizeof(V) * N});
+    return a;
+}
+
+template <typename V> aapdhg_status get_state_t(aapdhg_t h, unsigned char *buf) {
+    Prob<V> &P = prob<V>(h);
+    StateHeader hd;
+    std::memset(&hd, 0, sizeof(hd));
+    hd.magic = STATE_MAGIC;
+    hd.prec = h->prec;
+    hd.m = h->m;
+    hd.n = h->n;
+    hd.method = h->mp.method;
+    hd.mem = h->mp.mem;
+    hd.scaled = h->scaled ? 1 : 0;
+    hd.rings = P.DG ? 1 : 0;
+    hd.pw_snap = h->pw_snap ? 1 : 0;
+    hd.pw_base = (h->pw_dh_base && h->pw_base_valid) ? 1 : 0;
+    hd.dhat_mode = h->dhat_mode;
+    hd.nnz = h->nnz;
+    hd.N = h->N;
+    hd.Npad = h->Npad;
+    hd.pw_period = h->pw_period;
+    hd.pw_last_k = h->pw_last_k;
+    hd.bytes = (int64_t)state_bytes(h);
+    hd.lay[0] = h->lay[0];
+    hd.lay[1] = h->lay[1];
+    hd.mp = h->mp;
+    hd.pw_gamma = h->pw_gamma;
+    hd.pw_omega = h->pw_omega;
+    hd.pw_best_kkt = h->pw_best_kkt;
+    hd.tau_user = h->tau_user;
+    hd.sigma_user = h->sigma_user;
+    hd.time_used = h->time_used;
+    std::memcpy(buf, &hd, sizeof(hd));
+    size_t off = sizeof(hd);
+    for (auto &a : state_arrays<V>(h, hd.rings, hd.pw_snap, hd.pw_base)) {
+        CK(h, cudaMemcpyAsync(buf + off, a.first, a.second, cudaMemcpyDeviceToHost, h->stream));
+        off += a.second;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status set_state_t(aapdhg_t h, const unsigned char *buf, size_t bytes) {
+    StateHeader hd;
+    std::memcpy(&hd, buf, sizeof(hd));
+    if (hd.magic != STATE_MAGIC || hd.bytes != (int64_t)bytes)
+        return fail(h, AAPDHG_ERR_INVALID, "not a state blob of this library, or truncated");
+    if (hd.prec != h->prec || hd.m != h->m || hd.n != h->n || hd.nnz != h->nnz || hd.N != h->N ||
+        hd.Npad != h->Npad)
+        return fail(h, AAPDHG_ERR_INVALID, "state blob of another LP or precision");
+    if (hd.scaled != (h->scaled ? 1 : 0) || hd.method != h->mp.method || hd.mem != h->mp.mem ||
+        hd.pw_period != h->pw_period)
+        return fail(h, AAPDHG_ERR_INVALID,
+                    "state blob taken under another set-up (scaling, method, memory or primal weight period)");
+    if (hd.pw_snap && !h->pw_snap) return fail(h, AAPDHG_ERR_INVALID, "state blob needs the primal weight buffers");
+    aapdhg_status s;
+    if (hd.lay[0].sell_max != h->lay[0].sell_max || hd.lay[0].long_chunk != h->lay[0].long_chunk ||
+        hd.lay[1].sell_max != h->lay[1].sell_max || hd.lay[1].long_chunk != h->lay[1].long_chunk) {
+        const LayoutParams lay[2] = {hd.lay[0], hd.lay[1]};      // sums in the blob's order
+        if ((s = set_layout_t<V>(h, lay)) != AAPDHG_OK) return s;
+    }
+    if (hd.rings && (s = ensure_rings<V>(h, MAXM)) != AAPDHG_OK) return s;
+    if (hd.pw_base && !h->pw_dh_base) return fail(h, AAPDHG_ERR_INVALID, "state blob needs the primal weight buffers");
+    size_t off = sizeof(hd);
+    for (auto &a : state_arrays<V>(h, hd.rings, hd.pw_snap, hd.pw_base)) {
+        CK(h, cudaMemcpyAsync(a.first, buf + off, a.second, cudaMemcpyHostToDevice, h->stream));
+        off += a.second;
+    }
+    CK(h, cudaStreamSynchronize(h->stream));
+    h->mp = hd.mp;
+    h->have_steps = true;
+    h->pw_last_k = hd.pw_last_k;
+    h->pw_gamma = hd.pw_gamma;
+    h->pw_omega = hd.pw_omega;
+    h->pw_best_kkt = hd.pw_best_kkt;
+    h->pw_base_valid = hd.pw_base != 0;
+    h->tau_user = hd.tau_user;
+    h->sigma_user = hd.sigma_user;
+    h->time_used = hd.time_used;
+    h->dhat_mode = hd.dhat_mode;
+    drop_graphs(h);
+    return read_state(h);
+}
+
+}  // namespace
+
 extern "C" {
 
 aapdhg_status aapdhg_set_allocator(aapdhg_alloc_fn alloc, aapdhg_free_fn free_fn, void *ctx) {
@@ -1531,6 +1666,30 @@ aapdhg_status aapdhg_autotune_layout(aapdhg_t h, int32_t *layout4, double *avg_u
     }
     if (avg_us) for (int k = 0; k < 2 * AAPDHG_LAYOUT_CANDIDATES; ++k) avg_us[k] = h->lay_us[k];
     return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_state_size(aapdhg_t h, size_t *bytes) {
+    if (!h || !bytes) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    *bytes = state_bytes(h);
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_get_state(aapdhg_t h, void *buf, size_t bytes) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!buf || bytes != state_bytes(h))
+        return fail(h, AAPDHG_ERR_INVALID, "state buffer is NULL or not aapdhg_state_size bytes");
+    return h->prec == AAPDHG_FP64 ? get_state_t<double>(h, (unsigned char *)buf)
+                                  : get_state_t<float>(h, (unsigned char *)buf);
+}
+
+aapdhg_status aapdhg_set_state(aapdhg_t h, const void *buf, size_t bytes) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!buf || bytes < sizeof(StateHeader)) return fail(h, AAPDHG_ERR_INVALID, "state buffer is NULL or too short");
+    return h->prec == AAPDHG_FP64 ? set_state_t<double>(h, (const unsigned char *)buf, bytes)
+                                  : set_state_t<float>(h, (const unsigned char *)buf, bytes);
 }
 
 aapdhg_status aapdhg_set_time_limit(aapdhg_t h, double seconds) {

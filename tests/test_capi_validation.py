@@ -126,3 +126,14 @@ def test_kkt_noalloc_refuses_null_pointers():
         args = [dummy] * 14 + [None]
         args[i] = None
         assert L.aapdhg_kkt_noalloc(0, 20, *args) == binding.ERR_INVALID, i
+
+
+def test_state_calls_refuse_a_null_handle():
+    """The checkpoint calls check the handle before anything else."""
+    L = binding.load()
+    n = C.c_size_t(7)
+    assert L.aapdhg_state_size(None, C.byref(n)) == binding.ERR_INVALID
+    assert n.value == 7
+    buf = (C.c_uint8 * 64)()
+    assert L.aapdhg_get_state(None, buf, 64) == binding.ERR_INVALID
+    assert L.aapdhg_set_state(None, buf, 64) == binding.ERR_INVALID

@@ -495,8 +495,12 @@ template <typename V> void launch_dhat(aapdhg_t h, int mode, cudaStream_t s) {
 // Kernel kinds of the instrumentation.
 enum { KIND_XSTEP = 0, KIND_YSTEP = 1, KIND_MEMORY = 2, KIND_MIX = 3, KIND_GRAM = 4, NKIND = 5 };
 
+const char *const kKindName[NKIND] = {"aapdhg x-step", "aapdhg y-step", "aapdhg memory pass", "aapdhg AA mix",
+                                      "aapdhg Gram pass"};
+
 void mark_begin(aapdhg_t h, int kind) {
     h->launches += 1;
+    nvtxRangePushA(kKindName[kind]);
     if (!h->prof_on) return;
     const size_t need = 2 * (h->ev_kind.size() + 1);
     while (h->ev.size() < need) {
@@ -509,6 +513,7 @@ void mark_begin(aapdhg_t h, int kind) {
 }
 
 void mark_end(aapdhg_t h) {
+    nvtxRangePop();
     if (!h->prof_on || h->ev_kind.empty()) return;
     cudaEventRecord(h->ev[2 * h->ev_kind.size() - 1], h->stream);
 }
@@ -1455,6 +1460,7 @@ aapdhg_status aapdhg_create(int32_t m, int32_t n, int64_t nnz, const int64_t *ro
                             const int32_t *col_idx, const double *val, const int8_t *row_sense,
                             const double *q, const double *c, const double *lb, const double *ub,
                             int32_t precision, int32_t mem_kind, void *cuda_stream, aapdhg_t *out) {
+    NvtxRange range("aapdhg_create");
     if (!out) return fail(nullptr, AAPDHG_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (m < 0 || n < 1 || nnz < 0 || nnz >= ((int64_t)1 << 31))
@@ -1554,6 +1560,7 @@ aapdhg_status aapdhg_set_steps(aapdhg_t h, double tau, double sigma) {
 }
 
 aapdhg_status aapdhg_estimate_norm(aapdhg_t h, int32_t iters, uint64_t seed, double *norm) {
+    NvtxRange range("aapdhg_estimate_norm");
     if (!h || !norm || iters < 1) return h ? fail(h, AAPDHG_ERR_INVALID, "bad arguments") : AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     return h->prec == AAPDHG_FP64 ? estimate_norm_t<double>(h, iters, seed, norm)
@@ -1585,6 +1592,7 @@ aapdhg_status aapdhg_set_method(aapdhg_t h, int32_t method, int32_t m_A, double 
 }
 
 aapdhg_status aapdhg_set_scaling(aapdhg_t h, int32_t ruiz_iters, int32_t pock_chambolle) {
+    NvtxRange range("aapdhg_set_scaling");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (h->scaled || ruiz_iters < 0 || ruiz_iters > 1000)
@@ -1623,6 +1631,7 @@ aapdhg_status aapdhg_reset(aapdhg_t h) {
 
 aapdhg_status aapdhg_iterate(aapdhg_t h, int64_t max_iters, double tol, int32_t kkt_every,
                              int64_t *iters_done) {
+    NvtxRange range("aapdhg_iterate");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (!h->have_steps) return fail(h, AAPDHG_ERR_INVALID, "step sizes not set");
@@ -1654,6 +1663,7 @@ aapdhg_status aapdhg_set_layout(aapdhg_t h, const int32_t *layout4) {
 }
 
 aapdhg_status aapdhg_autotune_layout(aapdhg_t h, int32_t *layout4, double *avg_us) {
+    NvtxRange range("aapdhg_autotune_layout");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     aapdhg_status s = h->prec == AAPDHG_FP64 ? autotune_layout_t<double>(h) : autotune_layout_t<float>(h);
@@ -1676,6 +1686,7 @@ aapdhg_status aapdhg_state_size(aapdhg_t h, size_t *bytes) {
 }
 
 aapdhg_status aapdhg_get_state(aapdhg_t h, void *buf, size_t bytes) {
+    NvtxRange range("aapdhg_get_state");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (!buf || bytes != state_bytes(h))
@@ -1685,6 +1696,7 @@ aapdhg_status aapdhg_get_state(aapdhg_t h, void *buf, size_t bytes) {
 }
 
 aapdhg_status aapdhg_set_state(aapdhg_t h, const void *buf, size_t bytes) {
+    NvtxRange range("aapdhg_set_state");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (!buf || bytes < sizeof(StateHeader)) return fail(h, AAPDHG_ERR_INVALID, "state buffer is NULL or too short");
@@ -1834,6 +1846,7 @@ aapdhg_status aapdhg_set_primal_weight(aapdhg_t h, int64_t period, double theta,
 }
 
 aapdhg_status aapdhg_autotune(aapdhg_t h, int32_t *shape_x, int32_t *shape_y, double *avg_us) {
+    NvtxRange range("aapdhg_autotune");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     aapdhg_status s = h->prec == AAPDHG_FP64 ? autotune_t<double>(h) : autotune_t<float>(h);

@@ -171,8 +171,12 @@ template <class K> int boccupancy(K kernel) {
     return std::max(occ, 1);
 }
 
+const char *const kBKindName[BK_N] = {"aapdhg batch x-step", "aapdhg batch y-step", "aapdhg batch memory pass",
+                                      "aapdhg batch AA mix", "aapdhg batch KKT", "aapdhg batch Gram pass"};
+
 void bmark_begin(bh_t h, int kind) {
     h->launches += 1;
+    nvtxRangePushA(kBKindName[kind]);
     if (!h->prof_on) return;
     const size_t need = 2 * (h->ev_kind.size() + 1);
     while (h->ev.size() < need) {
@@ -185,6 +189,7 @@ void bmark_begin(bh_t h, int kind) {
 }
 
 void bmark_end(bh_t h) {
+    nvtxRangePop();
     if (!h->prof_on || h->ev_kind.empty()) return;
     cudaEventRecord(h->ev[2 * h->ev_kind.size() - 1], h->stream);
 }
@@ -875,6 +880,7 @@ aapdhg_status aapdhg_batch_create(int32_t nprob, const int32_t *m, const int32_t
                                   const int8_t *row_sense, const double *q, const double *c,
                                   const double *lb, const double *ub, int32_t precision,
                                   void *cuda_stream, aapdhg_batch_t *out) {
+    NvtxRange range("aapdhg_batch_create");
     if (!out) return bfail(nullptr, AAPDHG_ERR_INVALID, "out is NULL");
     *out = nullptr;
     if (nprob < 1 || nprob >= (1 << 25) || !m || !n || !nnz || !row_ptr)
@@ -1195,6 +1201,7 @@ aapdhg_status aapdhg_batch_set_tolerances(aapdhg_batch_t h, const double *tol) {
 
 aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double tol, int32_t kkt_every,
                                    int64_t *iters_done) {
+    NvtxRange range("aapdhg_batch_iterate");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (max_iters < 0 || kkt_every < 0 || !(tol >= 0))
@@ -1206,6 +1213,7 @@ aapdhg_status aapdhg_batch_iterate(aapdhg_batch_t h, int64_t max_iters, double t
 }
 
 aapdhg_status aapdhg_batch_launch(aapdhg_batch_t h, int64_t n_iters, double tol, int32_t kkt_every) {
+    NvtxRange range("aapdhg_batch_launch");
     if (!h) return AAPDHG_ERR_INVALID;
     if (h->sticky) return h->sticky;
     if (n_iters < 0 || kkt_every < 0 || !(tol >= 0))

@@ -11,9 +11,20 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace aaph {
+
+// NVTX range over a scope (header-only NVTX: free when no tool is attached).
+// The API calls and every kernel launch carry one, named by what they do.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 // Host threads for the set-up work of one LP with `work` entries: 1 below
 // 2^20 (thread start-up would dominate), else the hardware's, at most 16.

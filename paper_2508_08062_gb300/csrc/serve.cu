@@ -330,6 +330,7 @@ aapdhg_status aapdhg_server_submit(aapdhg_server_t s, int32_t m, int32_t n, int6
 }
 
 aapdhg_status aapdhg_server_step(aapdhg_server_t s, int32_t *running, int32_t *waiting) {
+    aaph::NvtxRange range("aapdhg_server_step");
     if (!s) return AAPDHG_ERR_INVALID;
     if (s->sticky) return s->sticky;
     aapdhg_status st = AAPDHG_OK;

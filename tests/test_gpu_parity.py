@@ -457,3 +457,29 @@ def test_mixed_primal_weight_converges():
         x, y = s.get_iterate()
     assert conv
     assert O.kkt(O.OracleLP.from_problem(P), x, y)["kkt"] <= 1.05e-4
+
+
+@pytest.mark.parametrize("prec,method", [("fp64", "aa"), ("mixed", "aa"), ("mixed", "faa")])
+def test_graph_chunks_equal_single_launches(prec, method):
+    """Full chunks of 64 iterations run as CUDA graphs; single iterations
+    launch every kernel directly.  Both must give the same iterates and
+    counters bit for bit, with AA steps both taken and refused along the way."""
+    P = lpgen.random_lp(400, 1000, nnz_per_row=6, frac_ge=0.3, frac_free=0.1, seed=17)
+    tau, sig = _steps(P)
+    res = []
+    for chunked in (True, False):
+        with _solver(P, prec) as s:
+            s.set_steps(tau, sig)
+            s.set_method(method, mem=6, D=10.0, eps=1.0)
+            s.set_task_shape(1, 1)        # the same grids: ||g|| summed in the same order
+            if chunked:
+                s.iterate(640, tol=0.0, kkt_every=64)
+            else:
+                for _ in range(640):
+                    s.iterate(1, tol=0.0, kkt_every=64)
+            x, y = s.get_iterate()
+            res.append((np.concatenate([x, y]), s.counters()))
+    (u1, c1), (u2, c2) = res
+    assert 0 < c1["aa_steps"] < 640, c1
+    assert c1 == c2
+    assert np.array_equal(u1, u2)

@@ -638,6 +638,7 @@ def run_batch(args):
 
     b = BatchSolver(members, precision="mixed", stream=stream)
     prepare(b)
+    layout = b.autotune_layout()   # slice width limit and long-row chunk of the packed K', K
     tuning = b.autotune()
     dev_uuid = str(torch.cuda.get_device_properties(local).uuid)
     dev_id = ("GPU-" + dev_uuid) if not dev_uuid.startswith("GPU-") else dev_uuid
@@ -788,6 +789,9 @@ def run_batch(args):
                        "task_shapes": {"x": tuning["shape_x"], "y": tuning["shape_y"],
                                        "x_us": [round(v, 1) for v in tuning["x_us"]],
                                        "y_us": [round(v, 1) for v in tuning["y_us"]]},
+                       "layout": {"x": list(layout["x"]), "y": list(layout["y"]),
+                                  "candidates_us": [[c["sell_max"], c["long_chunk"], round(c["x_us"], 1),
+                                                     round(c["y_us"], 1)] for c in layout["candidates"]]},
                        "l2": "inputs larger than L2 (no flush)"},
             "solved": solved, "batch_iterations": int(its),
             "member_iterations": {"p50": float(np.median(st[:, 0])), "max": int(st[:, 0].max()),

@@ -486,8 +486,8 @@ aapdhg_status aapdhg_batch_get_kkt(aapdhg_batch_t h, double *out6);
 aapdhg_status aapdhg_batch_get_status(aapdhg_batch_t h, int64_t *out6);
 
 /* CUDA-event timing of the batch kernels by kind: 0 half-step x, 1 half-step
- * y, 2 memory pass, 3 AA mix, 4 per-problem KKT, 5 per-problem Gram reduction
- * and m x m work; kind -1 gives in *launches
+ * y, 2 memory pass, 3 AA mix, 4 per-problem KKT, 5 per-problem push and
+ * safeguard, Gram pass and m x m work of the attempts; kind -1 gives in *launches
  * the number of kernels launched since profiling was last (re)set.          */
 aapdhg_status aapdhg_batch_profile_kernels(aapdhg_batch_t h, int32_t enable);
 aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, int64_t *launches,
@@ -497,6 +497,14 @@ aapdhg_status aapdhg_batch_get_kernel_profile(aapdhg_batch_t h, int32_t kind, in
 aapdhg_status aapdhg_batch_autotune(aapdhg_batch_t h, int32_t *shape_x, int32_t *shape_y,
                                     double *avg_us);
 aapdhg_status aapdhg_batch_set_task_shape(aapdhg_batch_t h, int32_t shape_x, int32_t shape_y);
+
+/* As aapdhg_set_layout / aapdhg_autotune_layout, on the packed batch: the
+ * layouts of the packed K' and K are rebuilt from the matrices on the device,
+ * every problem's rows in their own slices and chunks (so a problem's sums
+ * depend on the layout parameters only, not on the other problems), with the
+ * run state kept.  The default is (32, 1024) for both matrices.             */
+aapdhg_status aapdhg_batch_set_layout(aapdhg_batch_t h, const int32_t *layout4);
+aapdhg_status aapdhg_batch_autotune_layout(aapdhg_batch_t h, int32_t *layout4, double *avg_us);
 
 aapdhg_status aapdhg_batch_device_bytes(aapdhg_batch_t h, int64_t *bytes);
 const char *aapdhg_batch_last_error(aapdhg_batch_t h);

@@ -37,7 +37,8 @@ EXPORTS = ("aapdhg_set_allocator", "aapdhg_create", "aapdhg_set_steps", "aapdhg_
            "aapdhg_get_kernel_profile",
            "aapdhg_kkt_noalloc", "aapdhg_device_bytes", "aapdhg_last_error", "aapdhg_destroy",
            "aapdhg_autotune", "aapdhg_set_task_shape", "aapdhg_set_layout",
-           "aapdhg_autotune_layout", "aapdhg_batch_autotune",
+           "aapdhg_autotune_layout", "aapdhg_batch_autotune", "aapdhg_batch_set_layout",
+           "aapdhg_batch_autotune_layout",
            "aapdhg_set_primal_weight",
            "aapdhg_batch_set_task_shape", "aapdhg_batch_set_tolerances", "aapdhg_batch_launch",
            "aapdhg_batch_poll", "aapdhg_server_create", "aapdhg_server_submit",
@@ -111,6 +112,8 @@ def load(path: str = LIB_PATH):
     L.aapdhg_autotune_layout.argtypes = [vp, vp, vp]
     L.aapdhg_batch_autotune.argtypes = [vp, vp, vp, vp]
     L.aapdhg_batch_set_task_shape.argtypes = [vp, i32, i32]
+    L.aapdhg_batch_set_layout.argtypes = [vp, vp]
+    L.aapdhg_batch_autotune_layout.argtypes = [vp, vp, vp]
     L.aapdhg_batch_create.argtypes = [i32] + [vp] * 11 + [i32, vp, C.POINTER(vp)]
     L.aapdhg_batch_set_tolerances.argtypes = [vp, vp]
     L.aapdhg_batch_launch.argtypes = [vp, i64, f64, i32]
@@ -444,6 +447,23 @@ class BatchSolver:
 
     def set_task_shape(self, shape_x, shape_y):
         self._check(self._L.aapdhg_batch_set_task_shape(self._h, int(shape_x), int(shape_y)))
+
+    LAYOUT_CANDIDATES = Solver.LAYOUT_CANDIDATES
+
+    def set_layout(self, sell_max=32, long_chunk=1024, sell_max_y=None, long_chunk_y=None):
+        """As Solver.set_layout, on the packed K' and K."""
+        lay = np.array([sell_max, long_chunk, sell_max if sell_max_y is None else sell_max_y,
+                        long_chunk if long_chunk_y is None else long_chunk_y], dtype=np.int32)
+        self._check(self._L.aapdhg_batch_set_layout(self._h, _ptr(lay)))
+
+    def autotune_layout(self):
+        """As Solver.autotune_layout, on the packed K' and K."""
+        lay = np.zeros(4, dtype=np.int32)
+        us = np.zeros(2 * len(self.LAYOUT_CANDIDATES))
+        self._check(self._L.aapdhg_batch_autotune_layout(self._h, _ptr(lay), _ptr(us)))
+        return dict(x=(int(lay[0]), int(lay[1])), y=(int(lay[2]), int(lay[3])),
+                    candidates=[dict(sell_max=a, long_chunk=b, x_us=us[2 * i], y_us=us[2 * i + 1])
+                                for i, (a, b) in enumerate(self.LAYOUT_CANDIDATES)])
 
     def __init__(self, problems, precision: str = "mixed", stream=None, torch_memory: bool = True):
         import torch

@@ -916,10 +916,7 @@ template <typename V> aapdhg_status set_layout_t(aapdhg_t h, const LayoutParams 
     return AAPDHG_OK;
 }
 
-// Layout candidates of the layout tuner: slice width limit, long-row chunk.
-const LayoutParams kLayoutCand[AAPDHG_LAYOUT_CANDIDATES] = {{32, 1024}, {16, 1024}, {64, 1024},
-                                                            {128, 1024}, {32, 2048}, {64, 2048},
-                                                            {128, 2048}, {64, 4096}};
+static_assert(kNumLayoutCand == AAPDHG_LAYOUT_CANDIDATES, "layout candidates of the C ABI and the tuner differ");
 
 // Every candidate layout (the same for both matrices), with the task shapes
 // tuned on it.  The x-step reads only K' and the y-step only K, so K' keeps

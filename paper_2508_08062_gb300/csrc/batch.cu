@@ -87,6 +87,14 @@ struct aapdhg_batch_s {
     bool tuned = false, autotune = true;
     int32_t gridx[NSHAPE] = {}, gridy[NSHAPE] = {};
     double tune_us[2 * NSHAPE] = {};
+    // layouts of the packed K' and K (slice width limit, long-row chunk), the
+    // problems' row segments they are built from, and the device allocations
+    // of their layout parts, by matrix (0: K', 1: K)
+    LayoutParams lay[2];
+    std::vector<RowSeg> segs[2];
+    std::vector<void *> lay_ptrs[2];
+    double lay_us[2 * kNumLayoutCand] = {};
+    int64_t nnz_tot = 0;
     // primal weight update (off when pw_period = 0): per problem gamma, omega
     // and the lowest KKT at an update point (pw_w), the blend weight and
     // update flag of the last try, the snapshot
@@ -213,6 +221,23 @@ void bdrop_graphs(bh_t h) {
 // ---------------------------------------------------------------------------
 // set-up
 // ---------------------------------------------------------------------------
+// Grids per task shape for the common (non-KKT) half-step variants: all their
+// blocks resident.
+template <typename V> void bhalf_step_grids(bh_t h) {
+    Prob<V> &P = bprob<V>(h);
+    const int occx[NSHAPE] = {boccupancy(k_xstep_b<V, false, 0>), boccupancy(k_xstep_b<V, false, 1>),
+                              boccupancy(k_xstep_b<V, false, 2>), boccupancy(k_xstep_b<V, false, 3>),
+                              boccupancy(k_xstep_b<V, false, 4>)};
+    const int occy[NSHAPE] = {boccupancy(k_ystep_b<V, false, 0>), boccupancy(k_ystep_b<V, false, 1>),
+                              boccupancy(k_ystep_b<V, false, 2>), boccupancy(k_ystep_b<V, false, 3>),
+                              boccupancy(k_ystep_b<V, false, 4>)};
+    for (int sh = 0; sh < NSHAPE; ++sh) {
+        const int g = task_shape(sh).g;
+        h->gridx[sh] = bgrid(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
+        h->gridy[sh] = bgrid(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
+    }
+}
+
 template <typename V>
 aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vector<RowSeg> &segK,
                      const std::vector<RowSeg> &segKT, const std::vector<double> &cv,
@@ -227,12 +252,23 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     P.N = h->N;
     P.Npad = h->Npad;
     auto alloc = [&](size_t b) { return bdev_alloc(h, b); };
+    h->segs[0] = segKT;
+    h->segs[1] = segK;
+    h->nnz_tot = (int64_t)K.ci.size();
     for (int which = 0; which < 2 && ok; ++which) {
         LayoutHost L;
         const HostCSR &A = which ? K : KT;
-        if (!build_layout(A, which ? segK : segKT, L))
+        if (!build_layout(A, h->segs[which], L, h->lay[which]))
             return bfail(h, AAPDHG_ERR_INVALID, "packed SELL storage exceeds 2^31 entries");
-        if (!upload_csr<V>(A, L, which ? P.K : P.KT, alloc, h->stream)) ok = false;
+        CSRView<V> &view = which ? P.K : P.KT;
+        if (!upload_matrix<V>(A, view, alloc, h->stream)) ok = false;
+        std::vector<void *> &rec = h->lay_ptrs[which];
+        auto track = [&](size_t b) {
+            void *q = bdev_alloc(h, b);
+            if (q) rec.push_back(q);
+            return q;
+        };
+        if (!upload_layout<V>(L, view, track, h->stream)) ok = false;
     }
     auto to_v = [](const std::vector<double> &a) {
         std::vector<V> o(a.size());
@@ -252,18 +288,7 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     P.tr = Trace{0, nullptr, nullptr, nullptr, nullptr};
     P.st = nullptr;
     if (!P.UP || !P.dh || !P.g) ok = false;
-    // grids per task shape for the common (non-KKT) variants: all their blocks resident
-    const int occx[NSHAPE] = {boccupancy(k_xstep_b<V, false, 0>), boccupancy(k_xstep_b<V, false, 1>),
-                              boccupancy(k_xstep_b<V, false, 2>), boccupancy(k_xstep_b<V, false, 3>),
-                              boccupancy(k_xstep_b<V, false, 4>)};
-    const int occy[NSHAPE] = {boccupancy(k_ystep_b<V, false, 0>), boccupancy(k_ystep_b<V, false, 1>),
-                              boccupancy(k_ystep_b<V, false, 2>), boccupancy(k_ystep_b<V, false, 3>),
-                              boccupancy(k_ystep_b<V, false, 4>)};
-    for (int sh = 0; sh < NSHAPE; ++sh) {
-        const int g = task_shape(sh).g;
-        h->gridx[sh] = bgrid(h, (P.KT.ntasks(g) + WARPS - 1) / WARPS, occx[sh]);
-        h->gridy[sh] = bgrid(h, (P.K.ntasks(g) + WARPS - 1) / WARPS, occy[sh]);
-    }
+    bhalf_step_grids<V>(h);
     P.grid1 = h->gridx[0];
     P.grid2 = h->gridy[0];
 
@@ -498,6 +523,110 @@ template <typename V> aapdhg_status bautotune(bh_t h) {
     h->tuned = true;
     bdrop_graphs(h);
     return AAPDHG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Layouts of the packed K' and K (slice width limit, long-row chunk), rebuilt
+// from the matrices on the device with every problem's own row segments, as
+// the single-LP runtime does.  A problem's rows never share a slice with
+// another problem's, so each problem's sums depend on the layout parameters
+// only.  The run state is kept; the task shapes are tuned again.
+// ---------------------------------------------------------------------------
+void bdev_free_ptrs(bh_t h, const std::vector<void *> &ptrs) {
+    for (void *q : ptrs)
+        for (size_t i = 0; i < h->allocs.size(); ++i)
+            if (h->allocs[i].p == q) {
+                h->bytes -= (int64_t)h->allocs[i].bytes;
+                raw_free(q);
+                h->allocs.erase(h->allocs.begin() + (long)i);
+                break;
+            }
+}
+
+template <typename V> aapdhg_status bdownload_csr(bh_t h, const CSRView<V> &v, int64_t nnz, HostCSR &A) {
+    A.rows = v.rows;
+    A.rp.resize((size_t)v.rows + 1);
+    A.ci.resize((size_t)nnz);
+    A.val.resize((size_t)nnz);
+    std::vector<V> tmp((size_t)std::max<int64_t>(nnz, 1));
+    BCK(h, cudaMemcpyAsync(A.rp.data(), v.rp, sizeof(int32_t) * ((size_t)v.rows + 1), cudaMemcpyDeviceToHost,
+                           h->stream));
+    if (nnz > 0) {
+        BCK(h, cudaMemcpyAsync(A.ci.data(), v.ci, sizeof(int32_t) * (size_t)nnz, cudaMemcpyDeviceToHost, h->stream));
+        BCK(h, cudaMemcpyAsync(tmp.data(), v.val, sizeof(V) * (size_t)nnz, cudaMemcpyDeviceToHost, h->stream));
+    }
+    BCK(h, cudaStreamSynchronize(h->stream));
+    for (int64_t k = 0; k < nnz; ++k) A.val[k] = (double)tmp[k];
+    return AAPDHG_OK;
+}
+
+template <typename V> aapdhg_status bset_layout_t(bh_t h, const LayoutParams (&prm)[2]) {
+    Prob<V> &P = bprob<V>(h);
+    BCK(h, cudaStreamSynchronize(h->stream));
+    CSRView<V> nv[2] = {P.KT, P.K};
+    std::vector<void *> rec[2];
+    bool ok = true;
+    for (int w = 0; w < 2 && ok; ++w) {
+        HostCSR A;
+        aapdhg_status s = bdownload_csr<V>(h, nv[w], h->nnz_tot, A);
+        if (s != AAPDHG_OK) return s;
+        LayoutHost L;
+        if (!build_layout(A, h->segs[w], L, prm[w])) {
+            bdev_free_ptrs(h, rec[0]);
+            return bfail(h, AAPDHG_ERR_INVALID, "packed SELL storage exceeds 2^31 entries");
+        }
+        auto track = [&](size_t b) {
+            void *q = bdev_alloc(h, b);
+            if (q) rec[w].push_back(q);
+            return q;
+        };
+        if (!upload_layout<V>(L, nv[w], track, h->stream)) ok = false;
+    }
+    if (!ok) {
+        bdev_free_ptrs(h, rec[0]);
+        bdev_free_ptrs(h, rec[1]);
+        return bfail(h, AAPDHG_ERR_OOM, "layout: device allocation or copy failed");
+    }
+    bdev_free_ptrs(h, h->lay_ptrs[0]);
+    bdev_free_ptrs(h, h->lay_ptrs[1]);
+    h->lay_ptrs[0] = rec[0];
+    h->lay_ptrs[1] = rec[1];
+    P.KT = nv[0];
+    P.K = nv[1];
+    h->lay[0] = prm[0];
+    h->lay[1] = prm[1];
+    bhalf_step_grids<V>(h);
+    bset_shapes(h, 0, 0);
+    h->tuned = false;
+    bdrop_graphs(h);
+    return AAPDHG_OK;
+}
+
+// Every candidate layout for both matrices, with the task shapes tuned on it;
+// K' keeps the candidate with the fastest x-step, K the one with the fastest
+// y-step.
+template <typename V> aapdhg_status bautotune_layout_t(bh_t h) {
+    double bestx = INFINITY, besty = INFINITY;
+    int bx_i = 0, by_i = 0;
+    for (int c = 0; c < kNumLayoutCand; ++c) {
+        const LayoutParams both[2] = {kLayoutCand[c], kLayoutCand[c]};
+        aapdhg_status s = bset_layout_t<V>(h, both);
+        if (s == AAPDHG_OK) s = bautotune<V>(h);
+        if (s != AAPDHG_OK) return s;
+        double bx = INFINITY, by = INFINITY;
+        for (int sh = 0; sh < NSHAPE; ++sh) {
+            bx = std::min(bx, h->tune_us[sh]);
+            by = std::min(by, h->tune_us[NSHAPE + sh]);
+        }
+        h->lay_us[2 * c] = bx;
+        h->lay_us[2 * c + 1] = by;
+        if (bx < bestx) { bestx = bx; bx_i = c; }
+        if (by < besty) { besty = by; by_i = c; }
+    }
+    const LayoutParams chosen[2] = {kLayoutCand[bx_i], kLayoutCand[by_i]};
+    aapdhg_status s = bset_layout_t<V>(h, chosen);
+    if (s == AAPDHG_OK) s = bautotune<V>(h);
+    return s;
 }
 
 template <typename V> void blaunch_iteration(bh_t h, int64_t g, int mode) {
@@ -1316,6 +1445,38 @@ aapdhg_status aapdhg_batch_autotune(aapdhg_batch_t h, int32_t *shape_x, int32_t 
     if (shape_x) *shape_x = h->shape_x;
     if (shape_y) *shape_y = h->shape_y;
     if (avg_us) for (int k = 0; k < 2 * NSHAPE; ++k) avg_us[k] = h->tune_us[k];
+    return AAPDHG_OK;
+}
+
+aapdhg_status aapdhg_batch_set_layout(aapdhg_batch_t h, const int32_t *layout4) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    if (!layout4) return bfail(h, AAPDHG_ERR_INVALID, "layout4 is NULL");
+    LayoutParams prm[2];
+    for (int w = 0; w < 2; ++w) {
+        const int32_t sm = layout4[2 * w], lc = layout4[2 * w + 1];
+        if (sm < 1 || sm > 1024 || lc < 32 || lc > (1 << 20) || lc % 32)
+            return bfail(h, AAPDHG_ERR_INVALID,
+                         "layout: 1 <= sell_max <= 1024, long_chunk a multiple of 32 in [32, 2^20]");
+        prm[w].sell_max = sm;
+        prm[w].long_chunk = lc;
+    }
+    return h->prec == AAPDHG_FP64 ? bset_layout_t<double>(h, prm) : bset_layout_t<float>(h, prm);
+}
+
+aapdhg_status aapdhg_batch_autotune_layout(aapdhg_batch_t h, int32_t *layout4, double *avg_us) {
+    if (!h) return AAPDHG_ERR_INVALID;
+    if (h->sticky) return h->sticky;
+    NvtxRange range("aapdhg_batch_autotune_layout");
+    aapdhg_status s = h->prec == AAPDHG_FP64 ? bautotune_layout_t<double>(h) : bautotune_layout_t<float>(h);
+    if (s != AAPDHG_OK) return s;
+    if (layout4) {
+        layout4[0] = h->lay[0].sell_max;
+        layout4[1] = h->lay[0].long_chunk;
+        layout4[2] = h->lay[1].sell_max;
+        layout4[3] = h->lay[1].long_chunk;
+    }
+    if (avg_us) for (int k = 0; k < 2 * kNumLayoutCand; ++k) avg_us[k] = h->lay_us[k];
     return AAPDHG_OK;
 }
 

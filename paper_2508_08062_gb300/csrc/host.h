@@ -101,6 +101,12 @@ struct LayoutParams {
     int32_t long_chunk = aap::LONG_CHUNK;
 };
 
+// Candidates of the layout tuners (single LP and batch): slice width limit,
+// long-row chunk.
+constexpr int kNumLayoutCand = 8;
+constexpr LayoutParams kLayoutCand[kNumLayoutCand] = {{32, 1024}, {16, 1024}, {64, 1024},  {128, 1024},
+                                                      {32, 2048}, {64, 2048}, {128, 2048}, {64, 4096}};
+
 struct LayoutHost {
     int32_t n_long = 0, n_chunks = 0, n_slices = 0;
     int32_t long_chunk = aap::LONG_CHUNK;

@@ -444,3 +444,50 @@ def test_batch_primal_weight_rejects_parameters_out_of_range():
     with _batch([lpgen.tiny()]) as b:
         with pytest.raises(AAPDHGError, match="primal weight"):
             b.set_primal_weight(period=100, theta=1.5)
+
+
+@pytest.mark.parametrize("layout", [(1, 32), (64, 4096, 16, 64), (4, 96)])
+def test_fp64_batch_iterates_match_oracle_under_other_layouts(layout):
+    """The packed K' and K rebuilt with another slice width limit and chunk
+    length (every problem's rows in their own slices and chunks): the rows'
+    sums run in another order, so each member's FP64 iterates must still
+    follow its oracle trajectory within 1e-9, with the same AA/PDHG counts."""
+    iters = 60
+    probs = _members()
+    taus = np.array([0.9 / _norm(P) for P in probs])
+    refs = [O.solve(O.OracleLP.from_problem(P), _params(METHODS["aa5"], t), iters,
+                    rec_len=iters + 1) for P, t in zip(probs, taus)]
+    with _batch(probs) as b:
+        b.set_layout(*layout)
+        b.set_steps(taus, taus)
+        _set_method(b, _params(METHODS["aa5"], 1.0))
+        b.iterate(0)
+        for k in range(iters + 1):
+            for p, (x, y) in enumerate(b.get_iterate()):
+                err = _rel(np.concatenate([x, y]), refs[p].rec_u[k])
+                assert err <= FP64_TOL, (layout, p, k, err)
+            if k < iters:
+                b.iterate(1)
+        st = b.status()
+    for p, r in enumerate(refs):
+        assert st[p, 1] == r.aa_steps and st[p, 2] == r.pdhg_steps, (p, st[p])
+
+
+def test_batch_layout_autotuner_keeps_the_run():
+    from paper_2508_08062_gb300 import AAPDHGError
+    probs = _members()
+    taus = np.array([0.9 / _norm(P) for P in probs])
+    with _batch(probs, "mixed") as b:
+        b.set_steps(taus, taus)
+        b.set_method("aa", mem=5)
+        b.iterate(30)
+        before = b.status()[:, 0].copy()
+        t = b.autotune_layout()                  # the run state is kept
+        assert t["x"] in b.LAYOUT_CANDIDATES and t["y"] in b.LAYOUT_CANDIDATES
+        bx = min(c["x_us"] for c in t["candidates"])
+        assert [c["x_us"] for c in t["candidates"] if (c["sell_max"], c["long_chunk"]) == t["x"]][0] == bx
+        assert np.array_equal(b.status()[:, 0], before)
+        b.iterate(30)
+        assert np.all(b.status()[:, 0] == before + 30)
+        with pytest.raises(AAPDHGError):
+            b.set_layout(32, 100)                # not a multiple of 32

@@ -308,6 +308,8 @@ aapdhg_status bsetup(bh_t h, const HostCSR &K, const HostCSR &KT, const std::vec
     B.nprob = h->nprob;
     B.n_tot = h->n_tot;
     B.m_tot = h->m_tot;
+    if (chunk.size() > 65535)                // the Gram pass's grid has one row of blocks per chunk
+        return bfail(h, AAPDHG_ERR_INVALID, "batch too large: more than 65535 element chunks of 8192");
     B.nchunk = (int32_t)chunk.size();
     B.chunk = bput(h, chunk, &ok);
     B.pchunk0 = bput(h, pchunk0, &ok);
@@ -438,7 +440,7 @@ template <typename V, int MC> void blaunch_memory_mix(bh_t h, int cur) {
     bmark_begin(h, BK_GRAM);             // the push, and the Gram pass of the attempts
     k_gram_b<<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, fp64, h->mp);
     if (M > 0) {
-        k_gram_cols_b<V><<<dim3(B.nchunk, M), BLOCK, 0, h->stream>>>(P, B);
+        k_gram_cols_b<V><<<dim3(M, B.nchunk), BLOCK, 0, h->stream>>>(P, B);
         k_solve_b<<<h->nprob, 32, 0, h->stream>>>(h->bf, h->bd, fp64, h->mp);
         h->launches += 2;
     }

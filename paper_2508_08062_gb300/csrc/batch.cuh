@@ -63,6 +63,21 @@ template <typename V> struct BatchView {
 
 __device__ __forceinline__ bool stopped(const DevState *s) { return (s->done | s->error) != 0; }
 
+// Sum of p[c * stride] over chunks c0 <= c < c1 in chunk order (one thread),
+// with the loads of 8 chunks issued before their adds.
+__device__ __forceinline__ double ordered_chunk_sum(const double *p, int64_t stride, int c0, int c1) {
+    double v = 0.0;
+    for (int c = c0; c < c1; c += 8) {
+        double t[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) t[j] = c + j < c1 ? __ldcg(p + (int64_t)(c + j) * stride) : 0.0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+            if (c + j < c1) v += t[j];
+    }
+    return v;
+}
+
 // --------------------------------------------------------------------------
 // Half-step epilogues (eq. pdhg per row, step sizes of the row's problem)
 // --------------------------------------------------------------------------
@@ -364,7 +379,7 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
     const bool fresh = init || restart || M == 0;
     if (norm && lane < 4 && (!fresh || lane == 3)) {
         double v = 0.0;
-        for (int c = c0; c < c1; ++c) v += __ldcg(cpart + (int64_t)c * NBV + lane);
+        v = ordered_chunk_sum(cpart + lane, NBV, c0, c1);
         red[lane] = v;
     }
     __syncwarp();
@@ -416,7 +431,7 @@ __global__ void __launch_bounds__(32) k_gram_b(BatchView<float> Bf, BatchView<do
 // --------------------------------------------------------------------------
 // The Gram pass of the problems whose safeguard passed, in two kernels (the
 // single-LP k_gram's work, per problem):
-//   k_gram_cols_b  one block per (chunk, list position a) of such a problem:
+//   k_gram_cols_b  one block per (list position a, chunk) of such a problem:
 //                  the chunk's partial dot products of column a with its
 //                  partners in gram_pair_list (the columns b > a of its pairs
 //                  (a, b), then g^k for the right-hand side), into gpart at
@@ -435,10 +450,13 @@ constexpr int GRAM_PG = 8;                      // partners per pass over the ch
 template <typename V>
 __global__ void __launch_bounds__(BLOCK) k_gram_cols_b(Prob<V> P, BatchView<V> B) {
     constexpr int W = 16 / sizeof(V);
-    const int4 ch = B.chunk[blockIdx.x];
+    // blocks of one chunk are adjacent (x = list position), so the partners
+    // they share stay in L2
+    const int chunk = blockIdx.y;
+    const int4 ch = B.chunk[chunk];
     const DevState *st = B.stb + ch.x;
     if (stopped(st) || !st->init_done || !st->want_aa) return;
-    const int a = blockIdx.y, k = st->count;
+    const int a = blockIdx.x, k = st->count;
     if (a >= k) return;
     __shared__ int s_pidx[NSLOT];                  // list index of each partner's pair
     __shared__ const V *s_vec[NSLOT];              // partner vectors
@@ -495,7 +513,7 @@ __global__ void __launch_bounds__(BLOCK) k_gram_cols_b(Prob<V> P, BatchView<V> B
         if (threadIdx.x < GRAM_PG && j0 + threadIdx.x < np) {
             double v = 0.0;
             for (int w = 0; w < WARPS; ++w) v += Acc<V>::unpack(sh[w * GRAM_PG + threadIdx.x]);
-            B.gpart[(int64_t)blockIdx.x * GRAM_MAXPAIRS + s_pidx[j0 + threadIdx.x]] = v;
+            B.gpart[(int64_t)chunk * GRAM_MAXPAIRS + s_pidx[j0 + threadIdx.x]] = v;
         }
         __syncthreads();
     }
@@ -524,7 +542,7 @@ __global__ void __launch_bounds__(32) k_solve_b(BatchView<float> Bf, BatchView<d
     const int c0 = pchunk0[p], c1 = pchunk0[p + 1];
     for (int pr = lane; pr < np; pr += 32) {           // chunk order
         double v = 0.0;
-        for (int c = c0; c < c1; ++c) v += __ldcg(gpart + (int64_t)c * GRAM_MAXPAIRS + pr);
+        v = ordered_chunk_sum(gpart + pr, GRAM_MAXPAIRS, c0, c1);
         s_val[pr] = v;
     }
     __syncwarp();

@@ -55,6 +55,34 @@ def _with_long_row_and_column(seed=0, m=300, n=2500):
                            K.data, sense, base.l, base.u, name="long-row")
 
 
+def _with_mid_rows(seed=0, m=401, n=3001):
+    """Random LP in which 151 rows of K and 41 of its columns hold 33-128
+    entries (a few rows a little more): under the default layout they are
+    long rows of one chunk each, a warp task per row, next to the SELL slices
+    of the short rows."""
+    rng = np.random.default_rng(seed)
+    base = lpgen.random_lp(m, n, nnz_per_row=5, frac_ge=0.3, frac_free=0.1, seed=seed)
+    K = _Ksp(base).tocoo()
+    mid_rows = rng.choice(m, 151, replace=False)
+    keep = ~np.isin(K.row, mid_rows)
+    rows, cols, vals = [K.row[keep]], [K.col[keep]], [K.data[keep]]
+    for i in mid_rows:
+        c = rng.choice(n, int(rng.integers(33, 129)), replace=False)
+        rows.append(np.full(c.size, i)); cols.append(c); vals.append(rng.standard_normal(c.size))
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(m, n)).tocsc()
+    mid_cols = rng.choice(n, 41, replace=False)
+    A = A.tolil()
+    for j in mid_cols:
+        r = rng.choice(m, int(rng.integers(33, 100)), replace=False)
+        A[r, j] = rng.standard_normal((r.size, 1))
+    A = A.tocsr()
+    A.sum_duplicates()
+    A.sort_indices()
+    return lpgen.construct(rng, m, n, A.indptr.astype(np.int64), A.indices.astype(np.int32),
+                           A.data, base.sense, base.l, base.u, name="mid-rows")
+
+
 CASES = {
     "tiny_aa5": (lambda: lpgen.tiny(), dict(method=1, mem=5)),
     "tiny_faa5": (lambda: lpgen.tiny(), dict(method=2, mem=5)),
@@ -69,6 +97,8 @@ CASES = {
     "long_rows_faa10": (lambda: _with_long_row_and_column(1), dict(method=2, mem=10)),
     "identity_dhat": (lambda: lpgen.random_lp(50, 90, seed=9), dict(method=1, mem=3,
                                                                     dhat_mode=0, beta=0.5)),
+    "mid_rows_aa8": (lambda: _with_mid_rows(), dict(method=1, mem=8)),
+    "mid_rows_faa6": (lambda: _with_mid_rows(1), dict(method=2, mem=6)),
 }
 
 
@@ -300,9 +330,10 @@ def test_scaling_only_once_and_start_in_caller_units():
 # --------------------------------------------------------------------------
 # Autotuning of the half-step task shapes: the shape never changes a result
 # --------------------------------------------------------------------------
+@pytest.mark.parametrize("lp", ["long_row_and_column", "mid_rows"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_task_shapes_give_identical_iterates(prec):
-    P = _with_long_row_and_column(3)
+def test_task_shapes_give_identical_iterates(prec, lp):
+    P = _with_long_row_and_column(3) if lp == "long_row_and_column" else _with_mid_rows(3)
     tau, sig = _steps(P)
     got = []
     for shapes in ((0, 0), (1, 1), (2, 2), (3, 4), (4, 3), None):

@@ -545,7 +545,9 @@ def run_ours(args):
     # time to KKT <= 1e-4 (tested every 64 iterations) for AA-PDHG and plain PDHG
     ttt = None if (args.no_ttt or args.scale != 1.0) else time_to_tolerance(args, P, rank, stream, barrier)
     # the 256-LP batch to KKT <= 1e-4: solves/s and per-LP latency
-    batched = None if (args.no_ttt or args.scale != 1.0) else batched_to_tolerance(args, rank, stream, barrier)
+    batched = None
+    if not args.no_ttt and args.scale == 1.0 and args.workload == "large":
+        batched = batched_to_tolerance(args, rank, stream, barrier)
     p99 = None
     if batched and batched["time_to_tol_s"]["p99"] is not None:
         p99 = {"value": batched["time_to_tol_s"]["p99"], "unit": "s",

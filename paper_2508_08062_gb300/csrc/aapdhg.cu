@@ -737,7 +737,9 @@ template <typename V, int MC> void launch_memory_mix(aapdhg_t h, int mode, int f
     const int g5 = grid_for(h, (h->N + BLOCK * 4 - 1) / (BLOCK * 4), occ_mix);
     const int g3 = P.grid3;
     mark_begin(h, KIND_MEMORY);
-    k_memory<V><<<g3, BLOCK, 0, h->stream>>>(P, h->mp, mode, fin);
+    // fin with a memory: one more block runs the half-steps' final reduction
+    // beside the streaming blocks
+    k_memory<V><<<g3 + ((fin && M > 0) ? 1 : 0), BLOCK, 0, h->stream>>>(P, h->mp, mode, fin);
     mark_end(h);
     if (mode == MODE_ITER && M > 0) {
         mark_begin(h, KIND_GRAM);

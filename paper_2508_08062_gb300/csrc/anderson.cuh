@@ -356,10 +356,13 @@ static __device__ void push_finalize(DevState *st, const MethodParams &mp, int M
 
 // k_memory: see above.  mode INIT: only g^0 = u^1 - u^0 is written.
 // fin = 1 (iterations without a KKT test): the half-steps' final reduction
-// (||g^k||, the safeguard test; k_finalize's work) runs here, in the last
-// block, before the decisions that need it.  Without a KKT test the iteration
-// cannot stop, so the streaming part may run before that reduction; a NaN/Inf
-// it finds still stops the run before any AA step.
+// (||g^k||, the safeguard test; k_finalize's work) runs here too.  Without a
+// KKT test the iteration cannot stop, and the streaming part neither reads
+// nor writes what that reduction does, so the two run side by side: the grid
+// has one block more than P.grid3, and that block runs the reduction while
+// blocks 0 .. P.grid3 - 1 stream (on the restart path, which has no streaming
+// sums, it streams too and the last block runs the reduction).  A NaN/Inf the
+// reduction finds still stops the run before any AA step.
 template <typename V>
 __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, int mode, int fin) {
     constexpr int W = 16 / sizeof(V);
@@ -420,13 +423,16 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     __syncthreads();
     const int sn = s_new;
     const bool prev_acc = s_prev_acc != 0;
-    if (M > 0) {
+    const bool fin_block = blockIdx.x >= P.grid3;        // the extra block (fin = 1 only)
+    if (fin_block) {
+        finalize_T<V>(P, mp, mode, false);
+    } else if (M > 0) {
         Acc<V> acc[3];
         V *DGn = P.DG + (int64_t)sn * P.Npad;
         V *Wn = P.W + (int64_t)sn * P.Npad;
         const V beta = (V)mp.beta;
         const int64_t NV = P.N / W * W;
-        const int64_t stride = (int64_t)gridDim.x * BLOCK;
+        const int64_t stride = (int64_t)P.grid3 * BLOCK;
         for (int64_t e0 = (blockIdx.x * (int64_t)BLOCK + threadIdx.x) * W; e0 < NV; e0 += stride * W)
             push_elems<V, W>(P, e0, cur, prev_acc, beta, DGn, Wn, acc);
         for (int64_t e = NV + blockIdx.x * (int64_t)BLOCK + threadIdx.x; e < P.N; e += stride)
@@ -446,8 +452,10 @@ __global__ void __launch_bounds__(BLOCK) k_memory(Prob<V> P, MethodParams mp, in
     }
     if (!last_block(&st->cnt_ring)) return;
     if (fin) {
-        finalize_T<V>(P, mp, mode, false);
-        __syncthreads();
+        if ((int)gridDim.x == P.grid3) {                 // no extra block (M = 0)
+            finalize_T<V>(P, mp, mode, false);
+            __syncthreads();
+        }
         if (*reinterpret_cast<volatile int32_t *>(&st->error)) return;
     }
     if (M > 0) {

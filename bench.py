@@ -322,7 +322,7 @@ def batched_to_tolerance(args, rank, stream, barrier):
             times.append(time.perf_counter() - t1)
             iters.append(int(n))
             ok += int(c)
-    single = (ok / len(pick)) * nprob / (float(np.sum(times)) * nprob / len(pick))
+    single = ok / float(np.sum(times))          # converged solves per second of solver time
     rate = solved / wall
     return {"nprob": nprob, "rows": int(sum(P.m for P in members)),
             "cols": int(sum(P.n for P in members)), "nnz": int(sum(P.nnz for P in members)),
